@@ -1,0 +1,310 @@
+/*
+ * orc_core.c -- CPU ORACLE for the WHFast512 timestep.  TEST INFRASTRUCTURE ONLY.
+ *
+ * Only the tests, the package's smoke() check and the benchmark's CPU-baseline
+ * leg may load this code.  The product (the CUDA library) never calls it and
+ * shares no code, header, table or constant with it.
+ *
+ * A plain, scalar, FP64 restatement of the map the paper defines
+ * (Javaheri, Rein & Tamayo 2023, "WHFast512"): one Wisdom-Holman step in
+ * democratic heliocentric coordinates (Sec. 3.1, Eq. 1 and Eq. 2), built from
+ *   - the Kepler drift H_K (Sec. 3.2, Eq. 3): fixed 2 Halley + 2 Newton
+ *     iterations on the universal-variable Kepler equation, Stumpff series
+ *     truncated at 4 terms (Halley) and 8 (or 6, Appendix A) terms (Newton),
+ *   - the jump step H_J (Sec. 3.4, Eq. 6),
+ *   - the interaction kick H_I (Sec. 3.3, Eq. 5),
+ *   - the optional 1/r^2 "GR" potential centred on the star (Sec. 3.3, last
+ *     paragraphs).
+ * Loops are the obvious ones (planets in index order, pairs i < j, sequential
+ * sums); nothing is blocked, fused or reordered.  Build with -O2 -ffp-contract=off so that no
+ * multiply-add is contracted.
+ *
+ * Readings where the paper is silent (listed with reasons in the design notes):
+ *   - Kepler mu = G m_0 (H_K of Eq. 3 uses G m_0 m_i, not G(m_0+m_i)).
+ *   - initial guess X_0 = h/r_0 - eta_0 h^2 / (2 r_0^3) (second-order series).
+ *   - "T terms" = T terms each of the c_2 and c_3 series; c_0, c_1 follow from
+ *     c_0 = 1 - z c_2, c_1 = 1 - z c_3.
+ *   - f, g, fdot, gdot use G_n re-evaluated at the final X (T_N terms).
+ *   - GR: Phi(r) = -3 (G m_0)^2 / (c^2 r^2) per unit planet mass.  gr_mode 1
+ *     kicks v_i by h a_GR(Q_i) (canonical in these coordinates); gr_mode 2 also
+ *     subtracts sum_j (m_j/m_0) a_GR(Q_j) from every planet (the literal
+ *     reading of the back-reaction sentence).
+ *   - the two J(dt/2) half-steps are always applied separately.
+ *   - the interaction visits each unordered pair once (Newton's third law,
+ *     Sec. 3.3), in plain i < j order.
+ *   - a system whose step produces a non-finite value, or that starts a
+ *     Kepler drift with beta <= 0 (unbound; outside the solver's domain,
+ *     Sec. 3.2), is rolled back to the start of that step and frozen.
+ *
+ * This file is C99 and also compiles as C++ with ORC_REAL set to a counting
+ * number type (oracle/flopcount.cpp); that build only counts operations.
+ */
+#ifndef ORC_CORE_C
+#define ORC_CORE_C
+
+#include <math.h>
+#include <string.h>
+
+#ifndef ORC_REAL
+#define ORC_REAL double
+static double orc_sqrt(double x) { return sqrt(x); }
+static int orc_isfinite(double x) { return isfinite(x) != 0; }
+#endif
+typedef ORC_REAL orc_real;
+
+#define ORC_NMAX 8            /* planets per system */
+#define ORC_TMAX 12           /* longest Stumpff series supported */
+
+#define ORC_STATUS_NONFINITE 1
+#define ORC_STATUS_HYPERBOLIC 2
+
+typedef struct {
+    int gr_mode;         /* 0 off, 1 canonical, 2 with explicit back-reaction */
+    double c_light;      /* speed of light, code units */
+    int halley_iters;    /* 2 (Sec. 3.2) */
+    int halley_terms;    /* 4 (Sec. 3.2) */
+    int newton_iters;    /* 2 (Sec. 3.2) */
+    int newton_terms;    /* 8 (Sec. 3.2) or 6 (Appendix A) */
+} orc_options;
+
+/* One system in democratic heliocentric coordinates (Sec. 3.1).
+ * Q[i] is planet i's position relative to the star, v[i] = P_i / m_i its
+ * velocity relative to the barycentre; Xcm, Vcm, M describe H_0. */
+typedef struct {
+    int n;                      /* number of planets, 1..ORC_NMAX */
+    double m0;                  /* star mass */
+    double m[ORC_NMAX];
+    orc_real Q[ORC_NMAX][3];
+    orc_real v[ORC_NMAX][3];
+    double dt;
+    double M;                   /* total mass */
+    double Xcm[3], Vcm[3];      /* barycentre position (at t = 0) and velocity */
+    long long nstep;            /* completed steps; 0 = synchronized state */
+    int status;
+} orc_system;
+
+/* 1/k! for the Stumpff series: k! is exact in double for k <= 22, so one
+ * division rounds it correctly. */
+static double orc_inv_factorial(int k)
+{
+    double f = 1.0;
+    int i;
+    for (i = 2; i <= k; ++i) f *= (double)i;
+    return 1.0 / f;
+}
+
+/* Stumpff functions c_2(z), c_3(z) by their Taylor series truncated after
+ * `terms` terms, c_n(z) = sum_k (-z)^k / (n+2k)!, evaluated by Horner's rule
+ * (Sec. 3.2: series plus a precomputed table, no quarter-angle reduction). */
+static void orc_stumpff_c2c3(orc_real z, int terms, orc_real* c2, orc_real* c3)
+{
+    orc_real s2 = orc_inv_factorial(2 * terms);      /* k = terms-1: 1/(2+2k)! */
+    orc_real s3 = orc_inv_factorial(2 * terms + 1);  /* 1/(3+2k)! */
+    int k;
+    for (k = terms - 2; k >= 0; --k) {
+        s2 = orc_inv_factorial(2 * k + 2) - z * s2;
+        s3 = orc_inv_factorial(2 * k + 3) - z * s3;
+    }
+    *c2 = s2;
+    *c3 = s3;
+}
+
+/* Stiefel functions G_n(beta, X) = X^n c_n(beta X^2), n = 0..3, with
+ * c_0 = 1 - z c_2 and c_1 = 1 - z c_3. */
+static void orc_stiefel(orc_real beta, orc_real X, int terms, orc_real G[4])
+{
+    orc_real X2 = X * X;
+    orc_real z = beta * X2;
+    orc_real c2, c3;
+    orc_stumpff_c2c3(z, terms, &c2, &c3);
+    G[0] = 1.0 - z * c2;
+    G[1] = X * (1.0 - z * c3);
+    G[2] = X2 * c2;
+    G[3] = X2 * X * c3;
+}
+
+/* Kepler drift for one planet under H_K,i = P_i^2/2m_i - G m_0 m_i / Q_i
+ * (Sec. 3.2, Eq. 3) for time h with mu = G m_0 (G = 1).  Universal variable X,
+ * Kepler function F(X) = r_0 G_1 + eta_0 G_2 + mu G_3 - h, F' = r, F'' = dr/dX.
+ * Fixed iteration count, no convergence test, no branches.  Writes beta. */
+static void orc_kepler_drift(double mu, double h, orc_real Q[3], orc_real v[3],
+                             const orc_options* opt, orc_real* beta_out)
+{
+    orc_real r0 = orc_sqrt(Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2]);
+    orc_real eta0 = Q[0] * v[0] + Q[1] * v[1] + Q[2] * v[2];
+    orc_real v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    orc_real beta = 2.0 * mu / r0 - v2;
+    orc_real zeta0 = mu - beta * r0;
+    orc_real X = h / r0 - eta0 * h * h / (2.0 * r0 * r0 * r0);
+    orc_real G[4];
+    int it;
+    *beta_out = beta;
+
+    for (it = 0; it < opt->halley_iters; ++it) {           /* Halley's method */
+        orc_stiefel(beta, X, opt->halley_terms, G);
+        {
+            orc_real F = r0 * G[1] + eta0 * G[2] + mu * G[3] - h;
+            orc_real Fp = r0 * G[0] + eta0 * G[1] + mu * G[2];
+            orc_real Fpp = eta0 * G[0] + zeta0 * G[1];
+            X = X - 2.0 * F * Fp / (2.0 * Fp * Fp - F * Fpp);
+        }
+    }
+    for (it = 0; it < opt->newton_iters; ++it) {           /* Newton's method */
+        orc_stiefel(beta, X, opt->newton_terms, G);
+        {
+            orc_real F = r0 * G[1] + eta0 * G[2] + mu * G[3] - h;
+            orc_real Fp = r0 * G[0] + eta0 * G[1] + mu * G[2];
+            X = X - F / Fp;
+        }
+    }
+    orc_stiefel(beta, X, opt->newton_terms, G);             /* final X */
+    {
+        orc_real r = r0 * G[0] + eta0 * G[1] + mu * G[2];
+        orc_real f = 1.0 - mu * G[2] / r0;
+        orc_real g = h - mu * G[3];
+        orc_real fd = -mu * G[1] / (r * r0);
+        orc_real gd = 1.0 - mu * G[2] / r;
+        orc_real Qn[3], vn[3];
+        int c;
+        for (c = 0; c < 3; ++c) {
+            Qn[c] = f * Q[c] + g * v[c];
+            vn[c] = fd * Q[c] + gd * v[c];
+        }
+        for (c = 0; c < 3; ++c) {
+            Q[c] = Qn[c];
+            v[c] = vn[c];
+        }
+    }
+}
+
+/* Jump step H_J for time h (Sec. 3.4, Eq. 6): every planet's position moves by
+ * (h / m_0) sum_j P_j with P_j = m_j v_j summed over planets only; velocities
+ * are unchanged and the star does not move. */
+static void orc_jump(orc_system* s, double h)
+{
+    orc_real Psum[3] = {0.0, 0.0, 0.0};
+    int i, c;
+    for (i = 0; i < s->n; ++i)
+        for (c = 0; c < 3; ++c) Psum[c] = Psum[c] + s->m[i] * s->v[i][c];
+    for (i = 0; i < s->n; ++i)
+        for (c = 0; c < 3; ++c) s->Q[i][c] = s->Q[i][c] + h / s->m0 * Psum[c];
+}
+
+/* Interaction kick H_I for time h (Sec. 3.3, Eq. 5):
+ * a_i = -sum_{j != i} G m_j Q_ij / |Q_ij|^3 with Q_ij = Q_i - Q_j; v_i += h a_i.
+ * Each unordered pair i < j is visited once and gives both accelerations
+ * (Newton's third law, as Sec. 3.3 does to halve the square roots). */
+static void orc_interaction(orc_system* s, double h)
+{
+    orc_real a[ORC_NMAX][3];
+    int i, j, c;
+    for (i = 0; i < s->n; ++i)
+        for (c = 0; c < 3; ++c) a[i][c] = 0.0;
+    for (i = 0; i < s->n; ++i) {
+        for (j = i + 1; j < s->n; ++j) {
+            orc_real d[3], r2, r3, ki, kj;
+            for (c = 0; c < 3; ++c) d[c] = s->Q[i][c] - s->Q[j][c];
+            r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            r3 = r2 * orc_sqrt(r2);
+            ki = s->m[j] / r3;
+            kj = s->m[i] / r3;
+            for (c = 0; c < 3; ++c) {
+                a[i][c] = a[i][c] - ki * d[c];
+                a[j][c] = a[j][c] + kj * d[c];
+            }
+        }
+    }
+    for (i = 0; i < s->n; ++i)
+        for (c = 0; c < 3; ++c) s->v[i][c] = s->v[i][c] + h * a[i][c];
+}
+
+/* Acceleration from the 1/r^2 potential centred on the star (Sec. 3.3, GR
+ * paragraph; Nobili & Roxburgh 1986): Phi = -3 (G m_0)^2 / (c^2 r^2) per unit
+ * planet mass, a_GR(Q) = -grad Phi = -6 (G m_0)^2 Q / (c^2 |Q|^4). */
+static void orc_gr_acc(double m0, double c_light, const orc_real Q[3], orc_real a[3])
+{
+    orc_real r2 = Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2];
+    orc_real k = -6.0 * m0 * m0 / (c_light * c_light) / (r2 * r2);
+    int c;
+    for (c = 0; c < 3; ++c) a[c] = k * Q[c];
+}
+
+/* GR kick for time h.  gr_mode 1: v_i += h a_GR(Q_i).  gr_mode 2: the
+ * accelerations are scaled by m_j/m_0, summed, and the sum is subtracted from
+ * every planet's own term (the paper's back-reaction sentence). */
+static void orc_gr_kick(orc_system* s, double h, const orc_options* opt)
+{
+    orc_real a[ORC_NMAX][3];
+    int i, c;
+    for (i = 0; i < s->n; ++i) orc_gr_acc(s->m0, opt->c_light, s->Q[i], a[i]);
+    if (opt->gr_mode == 2) {
+        orc_real back[3] = {0.0, 0.0, 0.0};
+        for (i = 0; i < s->n; ++i)
+            for (c = 0; c < 3; ++c) back[c] = back[c] + s->m[i] / s->m0 * a[i][c];
+        for (i = 0; i < s->n; ++i)
+            for (c = 0; c < 3; ++c) a[i][c] = a[i][c] - back[c];
+    }
+    for (i = 0; i < s->n; ++i)
+        for (c = 0; c < 3; ++c) s->v[i][c] = s->v[i][c] + h * a[i][c];
+}
+
+static int orc_state_finite(const orc_system* s)
+{
+    int i, c;
+    for (i = 0; i < s->n; ++i)
+        for (c = 0; c < 3; ++c)
+            if (!orc_isfinite(s->Q[i][c]) || !orc_isfinite(s->v[i][c])) return 0;
+    return 1;
+}
+
+/* n Wisdom-Holman steps (Eq. 2) with the drifts of neighbouring steps fused:
+ * K(dt/2) on the first step after a synchronized state, K(dt) afterwards,
+ * then J(dt/2) I(dt) [GR] J(dt/2).  The trailing K(dt/2) is only applied to
+ * a copy for output (orc_synchronize), as in the paper's "keep unsynchronized"
+ * mode (Sec. 3.5 list). */
+static void orc_step(orc_system* s, long long n, const orc_options* opt)
+{
+    long long k;
+    for (k = 0; k < n; ++k) {
+        orc_real Qs[ORC_NMAX][3], vs[ORC_NMAX][3];
+        int i, bad = 0;
+        if (s->status) return;                          /* frozen */
+        memcpy(Qs, s->Q, sizeof(Qs));
+        memcpy(vs, s->v, sizeof(vs));
+        {
+            double hK = (s->nstep == 0) ? 0.5 * s->dt : s->dt;
+            for (i = 0; i < s->n; ++i) {
+                orc_real beta;
+                orc_kepler_drift(s->m0, hK, s->Q[i], s->v[i], opt, &beta);
+                if (!(beta > 0.0)) bad |= ORC_STATUS_HYPERBOLIC;
+            }
+        }
+        orc_jump(s, 0.5 * s->dt);
+        orc_interaction(s, s->dt);
+        if (opt->gr_mode) orc_gr_kick(s, s->dt, opt);
+        orc_jump(s, 0.5 * s->dt);
+        if (!orc_state_finite(s)) bad |= ORC_STATUS_NONFINITE;
+        if (bad) {
+            memcpy(s->Q, Qs, sizeof(Qs));
+            memcpy(s->v, vs, sizeof(vs));
+            s->status |= bad;
+            return;
+        }
+        s->nstep += 1;
+    }
+}
+
+/* Synchronized copy for output: the pending K(dt/2) (Sec. 3.5 list). */
+static void orc_synchronize(const orc_system* s, orc_system* out, const orc_options* opt)
+{
+    *out = *s;
+    if (s->nstep > 0) {
+        int i;
+        for (i = 0; i < s->n; ++i) {
+            orc_real beta;
+            orc_kepler_drift(s->m0, 0.5 * s->dt, out->Q[i], out->v[i], opt, &beta);
+        }
+    }
+}
+
+#endif /* ORC_CORE_C */

@@ -1,0 +1,198 @@
+"""Pins for the oracle's Kepler drift (Sec. 3.2, Eq. 3) and its Stumpff series.
+
+Everything here is checked against mathematics that does not depend on the
+oracle: closed forms of the Stumpff functions, and the exact two-body orbit of
+a massless test particle (the eccentric-anomaly solution of Kepler's equation,
+evaluated with mpmath at 40 digits).  A massless planet is the drift-only
+problem of the paper's Fig. 1: with m = 0 the jump and interaction steps do
+nothing, so n steps are n exact Kepler drifts.
+"""
+import os
+
+import mpmath as mp
+import numpy as np
+import pytest
+
+from paper_2307_05683_gb300 import inputs
+
+mp.mp.dps = 40
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "kepler_accuracy_criterion.txt")
+
+
+def _criterion():
+    out = {}
+    for line in open(GOLDEN):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            k, v = line.split()
+            out[k] = float(v)
+    return out
+
+
+def exact_state(a, e, M0, t, mu=1.0, inc=0.0):
+    """Exact Kepler orbit (pericentre on +x, then tilted about x by inc)."""
+    a, e, mu = mp.mpf(a), mp.mpf(e), mp.mpf(mu)
+    n = mp.sqrt(mu / a ** 3)
+    M = mp.mpf(M0) + n * mp.mpf(t)
+    E = mp.findroot(lambda E: E - e * mp.sin(E) - M, M)
+    x = a * (mp.cos(E) - e)
+    y = a * mp.sqrt(1 - e * e) * mp.sin(E)
+    r = a * (1 - e * mp.cos(E))
+    vx = -a * n * mp.sin(E) * a / r
+    vy = a * mp.sqrt(1 - e * e) * n * mp.cos(E) * a / r
+    ci, si = mp.cos(inc), mp.sin(inc)
+    Q = np.array([float(x), float(y * ci), float(y * si)])
+    v = np.array([float(vx), float(vy * ci), float(vy * si)])
+    return Q, v
+
+
+def semi_major_axis(Q, v, mu=1.0):
+    return 1.0 / (2.0 / np.linalg.norm(Q) - (v @ v) / mu)
+
+
+def particle_run(orc, a, e, M0, nsteps, dt, mu=1.0, **solver):
+    """Integrate one massless planet with the full map; return the
+    heliocentric synchronized state, status and time."""
+    o = orc.OracleEnsemble(1, 1, 0, **solver)
+    Q, v = exact_state(a, e, M0, 0.0, mu)
+    ens = inputs.Ensemble(np.array([[mu, 0.0]]), np.array([[[0, 0, 0], Q]]),
+                          np.array([[[0, 0, 0], v]]), np.array([1], np.int32), np.array([dt]))
+    o.init(ens)
+    o.step(nsteps)
+    pos, vel, st, t = o.read_state()
+    return pos[0, 1] - pos[0, 0], vel[0, 1] - vel[0, 0], int(st[0]), float(t[0])
+
+
+# ---------------------------------------------------------------- Stumpff --
+
+def _stumpff_exact(z):
+    z = mp.mpf(z)
+    if z == 0:
+        return mp.mpf(1) / 2, mp.mpf(1) / 6
+    if z > 0:
+        s = mp.sqrt(z)
+        return (1 - mp.cos(s)) / z, (s - mp.sin(s)) / (s ** 3)
+    s = mp.sqrt(-z)
+    return (mp.cosh(s) - 1) / (-z), (mp.sinh(s) - s) / (s ** 3)
+
+
+@pytest.mark.parametrize("terms", [4, 6, 8])
+@pytest.mark.parametrize("z", [-2.0, -0.5, -0.01, 0.0, 1e-9, 0.01, 0.3, 1.0, 1.5, 2.0])
+def test_stumpff_series_truncation(orc, z, terms):
+    """T-term series of c_2 and c_3 differ from the closed forms by the first
+    omitted term (alternating series, |z| small), plus rounding."""
+    c2, c3 = orc.stumpff(z, terms)
+    e2, e3 = _stumpff_exact(z)
+    omit2 = abs(mp.mpf(z) ** terms / mp.factorial(2 * terms + 2))
+    omit3 = abs(mp.mpf(z) ** terms / mp.factorial(2 * terms + 3))
+    assert abs(c2 - e2) <= 1.5 * omit2 + 4e-16
+    assert abs(c3 - e3) <= 1.5 * omit3 + 2e-16
+    if omit2 > 1e-13:      # the error is the omitted term itself: exactly T terms summed
+        assert abs(c2 - e2) >= 0.5 * omit2
+        assert abs(c3 - e3) >= 0.5 * omit3
+
+
+def test_stumpff_recurrence_identities(orc):
+    """c_0 = 1 - z c_2 and c_1 = 1 - z c_3 give cos and sin(x)/x (z = x^2)."""
+    for x in [0.05, 0.4, 0.9]:
+        c2, c3 = orc.stumpff(x * x, 8)
+        assert abs((1 - x * x * c2) - np.cos(x)) < 1e-15
+        assert abs((1 - x * x * c3) - np.sin(x) / x) < 1e-15
+
+
+# ---------------------------------------------------------------- drift --
+
+@pytest.mark.parametrize("a,e", [(0.387, 0.0), (0.387, 0.2056), (1.0, 0.5), (5.2, 0.05)])
+def test_single_drift_matches_exact_orbit(orc, a, e):
+    """One drift of 5 days from several phases lands on the exact orbit."""
+    o = orc.OracleEnsemble(1, 1)
+    h = 5 * inputs.DAY
+    for M0 in np.linspace(0, 2 * np.pi, 7)[:-1]:
+        Q0, v0 = exact_state(a, e, M0, 0.0, inc=0.3)
+        Q1, v1, beta = o.kepler(1.0, h, Q0, v0)
+        Qe, ve = exact_state(a, e, M0, h, inc=0.3)
+        assert beta == pytest.approx(1.0 / a, rel=1e-13)
+        assert np.linalg.norm(Q1 - Qe) <= 2e-15 * np.linalg.norm(Qe)
+        assert np.linalg.norm(v1 - ve) <= 4e-15 * np.linalg.norm(ve)
+
+
+def test_drift_uses_star_mass_only(orc):
+    """mu = G m_0 (H_K of Eq. 3): a heavier star changes the orbit accordingly,
+    and the planet's own mass does not enter the drift."""
+    o = orc.OracleEnsemble(1, 1)
+    h = 0.05
+    Q0, v0 = exact_state(1.0, 0.1, 0.4, 0.0, mu=2.5)
+    Q1, v1, _ = o.kepler(2.5, h, Q0, v0)
+    Qe, ve = exact_state(1.0, 0.1, 0.4, h, mu=2.5)
+    assert np.linalg.norm(Q1 - Qe) <= 2e-15 * np.linalg.norm(Qe)
+
+
+def test_drift_is_time_reversible(orc):
+    """Drift by h, flip v, drift by h, flip v: back to the start."""
+    o = orc.OracleEnsemble(1, 1)
+    Q0, v0 = exact_state(0.7, 0.3, 1.1, 0.0)
+    Q1, v1, _ = o.kepler(1.0, 0.08, Q0, v0)
+    Q2, v2, _ = o.kepler(1.0, 0.08, Q1, -v1)
+    assert np.allclose(Q2, Q0, rtol=0, atol=3e-16 * 0.7 * 4)
+    assert np.allclose(-v2, v0, rtol=0, atol=4e-15)
+
+
+def test_mercury_accuracy_criterion(orc):
+    """Appendix A requirement: at Mercury's a, 10 yr with a 5-day step, the
+    relative semi-major axis error of a test particle stays below 1e-13."""
+    c = _criterion()
+    a, dt = c["semi_major_axis_au"], c["timestep_days"] * inputs.DAY
+    n = int(round(c["duration_years"] * 365.25 / c["timestep_days"]))
+    for e in [0.0, 0.1, 0.2056, 0.4, 0.55, c["max_eccentricity_checked"]]:
+        for M0 in np.linspace(0, 2 * np.pi, 9)[:-1]:
+            Q, v, st, t = particle_run(orc, a, e, M0, n, dt)
+            assert st == 0
+            assert t == pytest.approx(n * dt)
+            assert abs(semi_major_axis(Q, v) / a - 1) < c["max_relative_a_error"], (e, M0)
+            Qe, _ = exact_state(a, e, M0, t)
+            assert np.linalg.norm(Q - Qe) < 1e-10 * np.linalg.norm(Qe)
+
+
+def test_semi_major_axis_error_unbiased(orc):
+    """Sec. 3.2 / Fig. 1: where the solver converges, the sign of the a error is
+    random across initial phases."""
+    dt = 5 * inputs.DAY
+    for e in [0.1, 0.3]:
+        signs = []
+        for M0 in np.linspace(0, 2 * np.pi, 17)[:-1]:
+            Q, v, _, _ = particle_run(orc, 0.387, e, M0, 730, dt)
+            signs.append(np.sign(semi_major_axis(Q, v) / 0.387 - 1))
+        assert 3 <= sum(s > 0 for s in signs) <= 13
+
+
+def test_fewer_iterations_or_terms_are_worse(orc):
+    """The fixed counts matter: one Newton step, or a 5-term final series,
+    misses the requirement at e = 0.65 (so the oracle really runs 2 + 2
+    iterations with 8-term Newton series)."""
+    dt = 5 * inputs.DAY
+    worst = {}
+    for name, solver in {"default": {}, "one_newton": {"newton_iters": 1},
+                         "five_terms": {"newton_terms": 5}}.items():
+        errs = []
+        for M0 in np.linspace(0, 2 * np.pi, 9)[:-1]:
+            Q, v, _, _ = particle_run(orc, 0.387, 0.65, M0, 730, dt, **solver)
+            errs.append(abs(semi_major_axis(Q, v) / 0.387 - 1))
+        worst[name] = max(errs)
+    assert worst["default"] < 1e-13
+    assert worst["one_newton"] > 3e-13
+    assert worst["five_terms"] > 1e-9
+
+
+def test_unbound_orbit_freezes_system(orc):
+    """beta <= 0 (outside the solver's domain, Sec. 3.2): the step is rolled back
+    and the system is frozen with the HYPERBOLIC status bit."""
+    o = orc.OracleEnsemble(1, 1)
+    Q = np.array([1.0, 0.0, 0.0])
+    v = np.array([0.0, 1.6, 0.0])          # v^2 > 2 mu / r
+    ens = inputs.Ensemble(np.array([[1.0, 0.0]]), np.array([[[0, 0, 0], Q]]),
+                          np.array([[[0, 0, 0], v]]), np.array([1], np.int32), np.array([0.01]))
+    o.init(ens)
+    o.step(5)
+    pos, vel, st, t = o.read_state()
+    assert st[0] == 2 and t[0] == 0.0
+    assert np.array_equal(pos[0, 1] - pos[0, 0], Q)
