@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark: FP64 system-steps/s of the Wisdom-Holman ensemble integrator.
+
+Workload (default): 4096 Solar-System-shaped systems (star + 8 planets, the
+8-planet template with masses and semi-major axes scaled by 1 + N(0, 1e-3),
+e and i perturbed by Rayleigh(1e-3), angles seeded), dt = P_Mercury / 20, GR
+term on.  One benchmark step = one whg_step call advancing every system by
+--chunk integrator steps (default 1e4; 100 benchmark steps = the full 1e6
+steps).  The state lives in registers during a launch, so there is no
+per-step memory traffic to cache; L2 is flushed (256 MB write) between timed
+steps anyway.
+
+Prints ONE JSON line.  --impl reference times the CPU oracle instead (rank 0).
+Multi-GPU (torchrun): each rank integrates its own ensemble of the same size
+(weak scaling, no data-path collective; a barrier and a max-reduction of the
+elapsed times only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2307_05683_gb300 import inputs  # noqa: E402
+
+METRIC = "8-planet FP64 system-steps/s on 1 GB300"
+UNIT = "system-steps/s"
+
+# Algorithmic FP64 operations per system-step (steady state, fused drift),
+# counted by the oracle's counting build (add/sub, mul, div, sqrt each one
+# operation); key (planets, newton_terms, gr_mode).  A CPU test keeps this
+# table equal to the oracle's count.
+ALG_FLOPS = {(8, 8, 1): 3360, (8, 8, 0): 3232, (8, 6, 1): 3168, (8, 8, 2): 3432}
+
+# FP64 peak from the unit counts and clocks: 152 SMs x 2 FP64 FMA lanes per
+# clock (1.25 TFLOP/s nominal / (152 x 2.07 GHz x 2)) x 2 flops x 2.07 GHz.
+SMS, FP64_LANES_PER_SM_CLK, SM_MAX_HZ = 152, 2, 2.07e9
+FP64_PEAK_TFLOPS = SMS * FP64_LANES_PER_SM_CLK * 2 * SM_MAX_HZ / 1e12
+
+PROFILE = os.path.join(ROOT, "profiles", "k_step_solar4096.md")
+
+
+def parse_args():
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["whg", "reference"], default="whg")
+    p.add_argument("--systems", type=int, default=4096)
+    p.add_argument("--chunk", type=int, default=10000, help="integrator steps per benchmark step")
+    p.add_argument("--gr-mode", type=int, default=1)
+    p.add_argument("--block-size", type=int, default=0)
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU work of the oracle sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--seed", type=int, default=2024)
+    return p.parse_args()
+
+
+def workload(args) -> dict:
+    return {"workload": f"{args.systems} Solar-System-shaped systems, star + 8 planets, FP64, "
+                        f"dt = P_Mercury/20, GR term {'on' if args.gr_mode else 'off'}",
+            "systems_per_gpu": args.systems, "planets": 8,
+            "integrator_steps_per_bench_step": args.chunk,
+            "gr_mode": args.gr_mode, "newton_terms": 8, "halley_terms": 4,
+            "l2": "state register-resident during a launch; 256 MB L2 flush between timed steps"}
+
+
+# ------------------------------------------------------------ environment --
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2307_05683_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(name.encode())
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "whg.h"), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per k_step launch from the committed ncu summary, or None if
+    the kernels changed since it was taken."""
+    if not os.path.exists(PROFILE):
+        return None
+    text = open(PROFILE).read()
+    m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ CPU oracle --
+
+def oracle_rate(ens, gr_mode: int, target_cpu_seconds: float, threads: int):
+    """Time the oracle (as it stands) on `threads` host threads over a bounded
+    sample of the ensemble: all systems, a step count sized for about
+    target_cpu_seconds of CPU work.  Returns (system-steps/s, sample text)."""
+    import oracle
+    oracle.build()
+    S = ens.n_systems
+    pilot = ens.subset(np.arange(min(S, 64)))
+    o = oracle.OracleEnsemble(pilot.n_systems, 8, gr_mode=gr_mode)
+    o.init(pilot)
+    t0 = time.perf_counter()
+    o.step(20)
+    per_core = pilot.n_systems * 20 / (time.perf_counter() - t0)
+    n = max(10, int(target_cpu_seconds * per_core / S))
+    o = oracle.OracleEnsemble(S, 8, gr_mode=gr_mode)
+    o.init(ens)
+    t0 = time.perf_counter()
+    used = o.run_threads(n, threads)
+    dt = time.perf_counter() - t0
+    return S * n / dt, f"{S} systems x {n} steps on {used} threads ({dt:.1f} s wall)", used
+
+
+# ------------------------------------------------------------ GPU arm --
+
+def run_whg(args):
+    import torch
+    from paper_2307_05683_gb300 import build, whg
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
+    build.build()
+    S, chunk = args.systems, args.chunk
+    ens = inputs.solar_ensemble(args.seed + rank, S)
+    stream = torch.cuda.Stream()
+    it = whg.Integrator(S, 8, gr_mode=args.gr_mode, block_size=args.block_size,
+                        stream=stream.cuda_stream)
+    it.init(ens)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            it.step(chunk)
+        stream.synchronize()
+        launches_per_step = None
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        gpu_idx = local
+        cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        if cvd and cvd.split(",")[0].strip().isdigit():
+            gpu_idx = int(cvd.split(",")[local].strip())
+        clocks = ClockSampler(gpu_idx)
+        clocks.start()
+        l0 = it.launches
+        for k in range(args.steps):
+            flush.add_(1.0)
+            ev[k][0].record(stream)
+            it.step(chunk)
+            ev[k][1].record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize()
+        launches = it.launches - l0
+        clock_info = clocks.stop()
+        if dist:
+            dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    worst = total_ms
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        worst = float(t.item())
+    value = world * S * chunk * args.steps / (worst / 1e3)
+    launches_per_step = launches / args.steps
+
+    # end to end through the public API: pinned host inputs -> init (H2D) ->
+    # step -> read_state (D2H), wall clock.
+    pinned = {}
+    for name in ("masses", "pos", "vel", "dt"):
+        a = getattr(ens, name)
+        t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+        t.numpy()[...] = a
+        pinned[name] = t
+    npl = torch.empty(S, dtype=torch.int32, pin_memory=True)
+    npl.numpy()[...] = ens.n_planets
+    out = {k: torch.empty(s, dtype=d, pin_memory=True) for k, s, d in
+           (("pos", (S, 9, 3), torch.float64), ("vel", (S, 9, 3), torch.float64),
+            ("status", (S,), torch.int32), ("t", (S,), torch.float64))}
+    h2d = sum(v.numel() * v.element_size() for v in pinned.values()) + npl.numel() * 4
+    d2h = sum(v.numel() * v.element_size() for v in out.values())
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        whg.whg_init(it.ctx, pinned["masses"].numpy(), pinned["pos"].numpy(), pinned["vel"].numpy(),
+                     npl.numpy(), pinned["dt"].numpy())
+        it.step(chunk)
+        whg.whg_read_state(it.ctx, out["pos"].numpy(), out["vel"].numpy(), out["status"].numpy(),
+                           out["t"].numpy())
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * S * chunk * args.e2e_steps / e2e_s
+    bad = int((out["status"].numpy() != 0).sum())
+
+    if rank != 0:
+        it.close()
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    flops = ALG_FLOPS[(8, 8, args.gr_mode)]
+    kernel_ms = total_ms / args.steps / max(launches_per_step, 1.0)
+    achieved = flops * S * (chunk / max(launches_per_step, 1.0)) / (kernel_ms / 1e3) / 1e12
+    dfma = whg.whg_measure_fp64_tflops(0.5)
+    roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+                "traffic": profiled_traffic(),
+                "kernel": "k_step<8,8,1> (FP64 pipe)",
+                "algorithmic_flops_per_system_step": flops,
+                "peak_basis": "recipe unit counts x clocks: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz",
+                "dfma_loop_measured_tflops": round(dfma, 4),
+                "frac_of_measured_dfma_loop": round(achieved / dfma, 4)}
+    line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Solar-System-shaped ensemble)",
+            "config": workload(args),
+            "roofline": roofline,
+            "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps,
+                    "api": "whg_init(host) + whg_step + whg_read_state(host)"},
+            "gpu_launches": int(launches),
+            "clocks": clock_info,
+            "systems_flagged": bad}
+    it.close()
+    if world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        rate, sample, used = oracle_rate(ens, args.gr_mode, args.cpu_seconds, threads)
+        line["cpu_baseline"] = {"value": round(rate, 1), "unit": UNIT, "cores": used, "kind": "oracle",
+                                "sample": sample}
+    if dist:
+        dist.destroy_process_group()
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ reference arm --
+
+def run_reference(args):
+    """The CPU oracle as it stands, on all host cores, rank 0 only."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    S = args.systems
+    ens = inputs.solar_ensemble(args.seed, S)
+    threads = os.cpu_count() or 1
+    o = oracle.OracleEnsemble(S, 8, gr_mode=args.gr_mode)
+    o.init(ens)
+    t0 = time.perf_counter()
+    o.run_threads(5, threads)
+    rate0 = S * 5 / (time.perf_counter() - t0)
+    # each reference step: every system advanced by n_ref steps, ~1 s of wall time,
+    # so --steps K --warmup W ends within a few minutes for K ~ 100
+    n_ref = max(1, int(rate0 * 1.0 / S))
+    for _ in range(args.warmup):
+        o.run_threads(n_ref, threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.run_threads(n_ref, threads)
+    wall = time.perf_counter() - t0
+    value = S * n_ref * args.steps / wall
+    sample = f"{S} systems x {n_ref} steps per benchmark step on {threads} threads"
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * wall / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Solar-System-shaped ensemble)", "config": workload(args),
+            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_whg(args)
+
+
+if __name__ == "__main__":
+    main()

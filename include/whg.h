@@ -1,0 +1,171 @@
+/*
+ * whg.h -- C ABI of libwhg, a GB300 (sm_103a) FP64 ensemble integrator for the
+ * WHFast512 timestep (Javaheri, Rein & Tamayo 2023).
+ *
+ * The library advances S independent planetary systems (a star plus 1..8
+ * planets each) with the Wisdom-Holman map in democratic heliocentric (DH)
+ * coordinates:
+ *     K(dt/2) . J(dt/2) . I(dt) . J(dt/2) . K(dt/2)           (Sec. 3.1, Eq. 2)
+ * with the Kepler drift K (Sec. 3.2, Eq. 3), the jump J (Sec. 3.4, Eq. 6), the
+ * interaction kick I (Sec. 3.3, Eq. 5) and the optional 1/r^2 GR term
+ * (Sec. 3.3).  Adjacent half drifts of consecutive steps are fused; output
+ * calls synchronize a copy and leave the live state unsynchronized
+ * ("keep unsynchronized", Sec. 3.5 list), so results are bitwise identical
+ * whatever the number of outputs or the way step counts are split into calls.
+ *
+ * Conventions (Sec. 3.5 list): G = 1; dt > 0 and fixed per system (integrate
+ * backwards by flipping velocities); masses are constant (call whg_init again
+ * to change masses or dt).  Massless planets are allowed.
+ *
+ * Arrays (row-major, FP64 unless stated; S = n_systems, N = max_planets,
+ * body 0 of every system is the star, bodies 1..n_planets[s] its planets,
+ * slots above n_planets[s] are ignored on input and zero on output):
+ *     masses [S][1+N]        pos [S][1+N][3]        vel [S][1+N][3]
+ * Positions and velocities are inertial-frame.  Raw state (DH, unsynchronized):
+ *     Q [S][N][3] heliocentric positions, v [S][N][3] barycentric velocities.
+ *
+ * Errors: every int-returning call returns WHG_OK (0) or a negative WHG_E*
+ * code and records a message retrievable with whg_last_error().  Numerical
+ * trouble inside one system is not an error: it sets that system's status
+ * bits (WHG_STATUS_*), rolls the system back to the start of the failing step
+ * and freezes it; all other systems continue.
+ *
+ * Threads and streams: a context is not thread-safe.  All device work of a
+ * context is issued on the stream given to whg_create / whg_set_stream (NULL =
+ * the legacy default stream).  Calls marked "async" return after enqueueing;
+ * calls taking host buffers block until their data has been copied.
+ */
+#ifndef WHG_H
+#define WHG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define WHG_OK 0
+#define WHG_EINVAL (-1)      /* invalid argument or input value */
+#define WHG_ECUDA (-2)       /* a CUDA runtime call or kernel launch failed */
+#define WHG_ENOMEM (-3)      /* device or host allocation failed */
+#define WHG_ESTATE (-4)      /* call out of order (e.g. step before init) */
+
+/* per-system status bits (frozen systems keep their last good state) */
+#define WHG_STATUS_NONFINITE 1   /* a step produced a non-finite coordinate */
+#define WHG_STATUS_HYPERBOLIC 2  /* a Kepler drift started with beta = 2 m0/r - v^2 <= 0
+                                    (unbound orbit: outside the fixed solver's domain, Sec. 3.2) */
+#define WHG_STATUS_INVALID 4     /* rejected input (device-pointer init only) */
+
+#define WHG_MAX_PLANETS 8
+
+typedef struct whg_ctx whg_ctx;
+
+typedef struct {
+    int gr_mode;              /* 0: no GR term.  1 (default): kick v_i by dt*a_GR(Q_i),
+                                 a_GR(Q) = -6 (G m0)^2 Q / (c^2 |Q|^4), the force of the
+                                 potential -3 (G m0)^2/(c^2 r^2) centred on the star
+                                 (Sec. 3.3, GR paragraph).  2: additionally subtract
+                                 sum_j (m_j/m0) a_GR(Q_j) from every planet (the
+                                 paper's back-reaction sentence read literally). */
+    double c_light;           /* speed of light in code units (AU, Msun, yr/2pi);
+                                 default 10065.32 */
+    int newton_terms;         /* Stumpff series terms in the Newton phase: 8 (default,
+                                 Sec. 3.2) or 6 (Appendix A).  The Halley phase always
+                                 uses 4 terms; 2 Halley + 2 Newton iterations (Sec. 3.2). */
+    int lanes_per_system;     /* 0 = auto (smallest power of two >= max_planets), else
+                                 1, 2, 4 or 8 (>= max_planets): GPU lanes per system */
+    int block_size;           /* CUDA threads per block, 0 = auto (multiple of 32) */
+    long long steps_per_launch; /* 0 = auto; bounds one kernel launch's length */
+} whg_options;
+
+/* Fill *opt with the defaults above. */
+void whg_default_options(whg_options* opt);
+
+/* Create a context for n_systems systems of at most max_planets (1..8)
+ * planets on the current CUDA device; allocates all device memory the
+ * context needs (owned by the library until whg_destroy).  opt may be NULL
+ * (defaults).  cuda_stream is a cudaStream_t or NULL.  On failure *out is
+ * NULL and whg_last_error(NULL) describes why. */
+int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options* opt,
+               void* cuda_stream);
+
+/* Set the stream used by all later calls on ctx. */
+int whg_set_stream(whg_ctx* ctx, void* cuda_stream);
+
+/* Initialise every system from HOST arrays (layouts above): converts to DH
+ * coordinates (Sec. 3.1: Q_i = x_i - x_0, v_i = u_i - V_cm) on the device and
+ * marks the state synchronized (the next step starts with K(dt/2)).
+ * n_planets [S] (int32) may be NULL (all systems have max_planets planets);
+ * dt [S] > 0.  Inputs are copied; the caller keeps ownership.  Returns
+ * WHG_EINVAL (nothing changed) if any system has m0 <= 0, a negative or
+ * non-finite mass, dt <= 0, n_planets outside 1..max_planets, a non-finite
+ * coordinate, or a planet at the star's position.  Blocks until copied. */
+int whg_init(whg_ctx* ctx, const double* masses, const double* pos, const double* vel,
+             const int* n_planets, const double* dt);
+
+/* As whg_init, but all pointers are DEVICE pointers (same layouts) on ctx's
+ * device, read on ctx's stream (async).  Invalid systems are not reported by
+ * the return value: they get WHG_STATUS_INVALID and stay frozen. */
+int whg_init_device(whg_ctx* ctx, const double* masses, const double* pos, const double* vel,
+                    const int* n_planets, const double* dt);
+
+/* Advance every live system by n_steps Wisdom-Holman steps (Eq. 2, drifts
+ * fused; async).  n_steps >= 0.  The split of work into kernel launches never
+ * changes results.  WHG_ESTATE before the first init. */
+int whg_step(whg_ctx* ctx, long long n_steps);
+
+/* Synchronized inertial state into HOST buffers pos, vel [S][1+N][3];
+ * status [S] (int32) and t [S] (time = steps done * dt) may be NULL.
+ * The pending K(dt/2) (Sec. 3.5 list) is applied to a copy; the live state is
+ * unchanged.  Blocks. */
+int whg_read_state(whg_ctx* ctx, double* pos, double* vel, int* status, double* t);
+
+/* As whg_read_state, into DEVICE buffers (async). */
+int whg_read_state_device(whg_ctx* ctx, double* pos, double* vel, int* status, double* t);
+
+/* Total energy H = H_0 + H_K + H_I + H_J (Eq. 1) of each system's
+ * synchronized state, plus sum_i m_i Phi_GR(Q_i) when gr_mode != 0; E [S] HOST
+ * buffer.  Blocks. */
+int whg_energy(whg_ctx* ctx, double* E);
+
+/* As whg_energy, into a DEVICE buffer (async). */
+int whg_energy_device(whg_ctx* ctx, double* E);
+
+/* Raw unsynchronized DH state for bitwise checkpoint / resume, HOST buffers:
+ * Q, v [S][N][3]; nstep [S] (int64, steps done; 0 = synchronized);
+ * status [S] (int32).  get blocks; set copies and returns (async after copy).
+ * set requires a prior init (masses, dt and barycentre come from it). */
+int whg_get_raw(whg_ctx* ctx, double* Q, double* v, long long* nstep, int* status);
+int whg_set_raw(whg_ctx* ctx, const double* Q, const double* v, const long long* nstep,
+                const int* status);
+
+/* Wait until all work issued on ctx's stream has finished. */
+int whg_synchronize(whg_ctx* ctx);
+
+/* Number of the library's kernel launches issued on ctx so far. */
+long long whg_launch_count(const whg_ctx* ctx);
+
+/* Message for the last error on ctx (or of the last failed whg_create, ctx
+ * NULL).  Valid until the next call on ctx. */
+const char* whg_last_error(const whg_ctx* ctx);
+
+/* Free all resources of ctx (NULL is a no-op).  Synchronizes its stream. */
+void whg_destroy(whg_ctx* ctx);
+
+/* ---- diagnostics (not part of the integration path) -------------------- */
+
+/* FP64 pipe throughput: runs a dependent-FMA loop on every SM of the current
+ * device for about `seconds` and returns achieved FP64 TFLOP/s (FMA = 2
+ * flops).  Blocks. */
+int whg_measure_fp64_tflops(double seconds, double* tflops);
+
+/* The library's own reciprocal and reciprocal square root next to CUDA's, for
+ * testing: out [4][n] DEVICE buffer receives rcp_own(x), 1/x (CUDA, IEEE),
+ * rsqrt_own(x), rsqrt(x) (CUDA) for the n DEVICE inputs x (x > 0 for the
+ * square roots).  Blocks. */
+int whg_test_special(const double* x, int n, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WHG_H */

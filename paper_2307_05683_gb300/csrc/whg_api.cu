@@ -1,0 +1,428 @@
+// whg_api.cu -- host side of libwhg: the C ABI declared in include/whg.h.
+//
+// A context owns the ensemble's device state (structure of arrays, lane index
+// s * G + p) and staging buffers for host I/O.  Every operation is a kernel on
+// the context's stream; host-pointer calls add one cudaMemcpyAsync each way and
+// wait for it.  Inputs given as host arrays are validated on the host.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "whg_internal.h"
+
+struct whg_ctx {
+    int S, Nmax, G, S_pad, block;
+    whg_options opt;
+    cudaStream_t stream;
+    int device;
+    bool initialized;
+    long long launches;
+    WhgState st;
+    const WhgKernels* kern;
+    // staging for host I/O (device memory)
+    double* stage_d;          // S * (7 * (1 + Nmax) + 1) doubles
+    int* stage_i;             // 2 * S ints
+    long long* stage_l;       // S int64
+    char err[256];
+};
+
+namespace {
+
+thread_local char g_create_err[256] = "";
+
+int fail(whg_ctx* c, int code, const char* fmt, ...)
+{
+    char* dst = c ? c->err : g_create_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 256, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(whg_ctx* c, cudaError_t e, const char* what)
+{
+    return fail(c, WHG_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define WHG_CUDA(ctx, call)                                          \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);   \
+    } while (0)
+
+const WhgKernels* kernels_for(int G)
+{
+    switch (G) {
+    case 1: return &whg_kernels_g1;
+    case 2: return &whg_kernels_g2;
+    case 4: return &whg_kernels_g4;
+    case 8: return &whg_kernels_g8;
+    default: return nullptr;
+    }
+}
+
+WhgLaunch launch_cfg(const whg_ctx* c)
+{
+    WhgLaunch l;
+    l.block = c->block;
+    l.grid = (int)(((long long)c->S_pad * c->G) / c->block);
+    l.stream = c->stream;
+    return l;
+}
+
+bool finite(double x) { return std::isfinite(x); }
+
+// Host-side validation of inertial inputs (returns system index of the first
+// bad system, or -1).
+int validate(const whg_ctx* c, const double* m, const double* x, const double* u, const int* np,
+             const double* dt, char* why, size_t nwhy)
+{
+    const int B = 1 + c->Nmax;
+    for (int s = 0; s < c->S; ++s) {
+        const int n = np ? np[s] : c->Nmax;
+        const double* ms = m + (size_t)s * B;
+        const double* xs = x + (size_t)s * B * 3;
+        const double* us = u + (size_t)s * B * 3;
+        if (n < 1 || n > c->Nmax) { snprintf(why, nwhy, "n_planets=%d outside 1..%d", n, c->Nmax); return s; }
+        if (!(dt[s] > 0.0) || !finite(dt[s])) { snprintf(why, nwhy, "dt=%g must be finite and > 0", dt[s]); return s; }
+        if (!(ms[0] > 0.0) || !finite(ms[0])) { snprintf(why, nwhy, "star mass %g must be > 0", ms[0]); return s; }
+        for (int k = 0; k <= n; ++k) {
+            if (!(ms[k] >= 0.0) || !finite(ms[k])) { snprintf(why, nwhy, "mass of body %d is %g", k, ms[k]); return s; }
+            for (int d = 0; d < 3; ++d)
+                if (!finite(xs[3 * k + d]) || !finite(us[3 * k + d])) {
+                    snprintf(why, nwhy, "non-finite coordinate of body %d", k);
+                    return s;
+                }
+            if (k > 0 && xs[3 * k] == xs[0] && xs[3 * k + 1] == xs[1] && xs[3 * k + 2] == xs[2]) {
+                snprintf(why, nwhy, "planet %d sits on the star", k);
+                return s;
+            }
+        }
+    }
+    return -1;
+}
+
+int launch_check(whg_ctx* c, cudaError_t e, const char* what)
+{
+    if (e != cudaSuccess) return cuda_fail(c, e, what);
+    c->launches += 1;
+    return WHG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void whg_default_options(whg_options* opt)
+{
+    if (!opt) return;
+    opt->gr_mode = 1;
+    opt->c_light = 173.1446326742403 / 0.01720209895;
+    opt->newton_terms = 8;
+    opt->lanes_per_system = 0;
+    opt->block_size = 0;
+    opt->steps_per_launch = 0;
+}
+
+int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options* opt_in,
+               void* cuda_stream)
+{
+    if (!out) return fail(nullptr, WHG_EINVAL, "out is NULL");
+    *out = nullptr;
+    whg_options opt;
+    whg_default_options(&opt);
+    if (opt_in) opt = *opt_in;
+    if (n_systems < 1) return fail(nullptr, WHG_EINVAL, "n_systems=%d must be >= 1", n_systems);
+    if (max_planets < 1 || max_planets > WHG_MAX_PLANETS)
+        return fail(nullptr, WHG_EINVAL, "max_planets=%d outside 1..%d", max_planets, WHG_MAX_PLANETS);
+    if (opt.gr_mode < 0 || opt.gr_mode > 2) return fail(nullptr, WHG_EINVAL, "gr_mode=%d", opt.gr_mode);
+    if (opt.gr_mode && !(opt.c_light > 0.0 && std::isfinite(opt.c_light)))
+        return fail(nullptr, WHG_EINVAL, "c_light=%g must be > 0", opt.c_light);
+    if (opt.newton_terms != 6 && opt.newton_terms != 8)
+        return fail(nullptr, WHG_EINVAL, "newton_terms=%d must be 6 or 8", opt.newton_terms);
+    int G = opt.lanes_per_system;
+    if (G == 0) {
+        G = 1;
+        while (G < max_planets) G <<= 1;
+    }
+    if (!kernels_for(G) || G < max_planets)
+        return fail(nullptr, WHG_EINVAL, "lanes_per_system=%d must be 1, 2, 4 or 8 and >= max_planets",
+                    opt.lanes_per_system);
+    int block = opt.block_size ? opt.block_size : 32;
+    if (block < 32 || block > WHG_MAX_BLOCK || block % 32)
+        return fail(nullptr, WHG_EINVAL, "block_size=%d must be a multiple of 32 in 32..%d", block,
+                    WHG_MAX_BLOCK);
+    if (opt.steps_per_launch < 0)
+        return fail(nullptr, WHG_EINVAL, "steps_per_launch=%lld must be >= 0", opt.steps_per_launch);
+
+    whg_ctx* c = new (std::nothrow) whg_ctx();
+    if (!c) return fail(nullptr, WHG_ENOMEM, "host allocation failed");
+    c->S = n_systems;
+    c->Nmax = max_planets;
+    c->G = G;
+    c->block = block;
+    const int per_block = block / G;
+    c->S_pad = (int)(((long long)n_systems + per_block - 1) / per_block * per_block);
+    c->opt = opt;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->kern = kernels_for(G);
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(nullptr, WHG_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    }
+
+    const size_t L = (size_t)c->S_pad * G, P = (size_t)c->S_pad;
+    const size_t nd = 7 * L + 9 * P;
+    void* base = nullptr;
+    size_t bytes = nd * sizeof(double) + 2 * P * sizeof(int) + P * sizeof(long long);
+    e = cudaMalloc(&base, bytes);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(nullptr, WHG_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    double* d = (double*)base;
+    WhgState& st = c->st;
+    st.m = d; d += L;
+    st.qx = d; d += L;
+    st.qy = d; d += L;
+    st.qz = d; d += L;
+    st.vx = d; d += L;
+    st.vy = d; d += L;
+    st.vz = d; d += L;
+    st.m0 = d; d += P;
+    st.dt = d; d += P;
+    st.M = d; d += P;
+    st.xcm = d; d += 3 * P;
+    st.vcm = d; d += 3 * P;
+    long long* ll = (long long*)d;
+    st.nstep = ll; ll += P;
+    int* ip = (int*)ll;
+    st.nplan = ip; ip += P;
+    st.status = ip;
+    st.S = n_systems;
+    st.S_pad = c->S_pad;
+    st.Nmax = max_planets;
+    st.c_light = opt.c_light;
+
+    const size_t B = 1 + (size_t)max_planets;
+    const size_t sd = (size_t)n_systems * (7 * B + 1);
+    const size_t sbytes = sd * sizeof(double) + 2 * (size_t)n_systems * sizeof(int) +
+                          (size_t)n_systems * sizeof(long long);
+    void* sbase = nullptr;
+    e = cudaMalloc(&sbase, sbytes);
+    if (e != cudaSuccess) {
+        cudaFree(base);
+        delete c;
+        return fail(nullptr, WHG_ENOMEM, "cudaMalloc(%zu): %s", sbytes, cudaGetErrorString(e));
+    }
+    c->stage_d = (double*)sbase;
+    c->stage_l = (long long*)(c->stage_d + sd);
+    c->stage_i = (int*)(c->stage_l + n_systems);
+    *out = c;
+    return WHG_OK;
+}
+
+int whg_set_stream(whg_ctx* c, void* cuda_stream)
+{
+    if (!c) return WHG_EINVAL;
+    c->stream = (cudaStream_t)cuda_stream;
+    return WHG_OK;
+}
+
+static int init_common(whg_ctx* c, const WhgIn& in)
+{
+    WhgLaunch l = launch_cfg(c);
+    int rc = launch_check(c, c->kern->init(c->st, in, l), "init kernel");
+    if (rc) return rc;
+    c->initialized = true;
+    return WHG_OK;
+}
+
+int whg_init(whg_ctx* c, const double* masses, const double* pos, const double* vel,
+             const int* n_planets, const double* dt)
+{
+    if (!c) return WHG_EINVAL;
+    if (!masses || !pos || !vel || !dt) return fail(c, WHG_EINVAL, "null input array");
+    char why[160];
+    int bad = validate(c, masses, pos, vel, n_planets, dt, why, sizeof why);
+    if (bad >= 0) return fail(c, WHG_EINVAL, "system %d: %s", bad, why);
+    const size_t S = c->S, B = 1 + (size_t)c->Nmax;
+    double* dm = c->stage_d;
+    double* dx = dm + S * B;
+    double* du = dx + S * B * 3;
+    double* ddt = du + S * B * 3;
+    WHG_CUDA(c, cudaMemcpyAsync(dm, masses, S * B * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    WHG_CUDA(c, cudaMemcpyAsync(dx, pos, S * B * 3 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    WHG_CUDA(c, cudaMemcpyAsync(du, vel, S * B * 3 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    WHG_CUDA(c, cudaMemcpyAsync(ddt, dt, S * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    int* dn = nullptr;
+    if (n_planets) {
+        dn = c->stage_i;
+        WHG_CUDA(c, cudaMemcpyAsync(dn, n_planets, S * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    }
+    WhgIn in{dm, dx, du, dn, ddt};
+    int rc = init_common(c, in);
+    if (rc) return rc;
+    WHG_CUDA(c, cudaStreamSynchronize(c->stream));      // host buffers may be reused on return
+    return WHG_OK;
+}
+
+int whg_init_device(whg_ctx* c, const double* masses, const double* pos, const double* vel,
+                    const int* n_planets, const double* dt)
+{
+    if (!c) return WHG_EINVAL;
+    if (!masses || !pos || !vel || !dt) return fail(c, WHG_EINVAL, "null input array");
+    WhgIn in{masses, pos, vel, n_planets, dt};
+    return init_common(c, in);
+}
+
+int whg_step(whg_ctx* c, long long n)
+{
+    if (!c) return WHG_EINVAL;
+    if (!c->initialized) return fail(c, WHG_ESTATE, "whg_step before whg_init");
+    if (n < 0) return fail(c, WHG_EINVAL, "n_steps=%lld must be >= 0", n);
+    long long chunk = c->opt.steps_per_launch;
+    if (chunk <= 0) {
+        // about 5e7 system-steps per launch (a few tenths of a second)
+        chunk = 50000000LL / (long long)c->S_pad;
+        if (chunk < 1) chunk = 1;
+    }
+    WhgLaunch l = launch_cfg(c);
+    while (n > 0) {
+        const long long k = n < chunk ? n : chunk;
+        int rc = launch_check(c, c->kern->step(c->st, k, c->opt.newton_terms, c->opt.gr_mode, l),
+                              "step kernel");
+        if (rc) return rc;
+        n -= k;
+    }
+    return WHG_OK;
+}
+
+int whg_read_state_device(whg_ctx* c, double* pos, double* vel, int* status, double* t)
+{
+    if (!c) return WHG_EINVAL;
+    if (!c->initialized) return fail(c, WHG_ESTATE, "read before whg_init");
+    WhgOut o{};
+    o.pos = pos;
+    o.vel = vel;
+    o.status = status;
+    o.t = t;
+    return launch_check(c, c->kern->read(c->st, o, c->opt.newton_terms, launch_cfg(c)), "read kernel");
+}
+
+int whg_read_state(whg_ctx* c, double* pos, double* vel, int* status, double* t)
+{
+    if (!c) return WHG_EINVAL;
+    if (!pos || !vel) return fail(c, WHG_EINVAL, "null output array");
+    const size_t S = c->S, B = 1 + (size_t)c->Nmax;
+    double* dx = c->stage_d;
+    double* du = dx + S * B * 3;
+    double* dtm = du + S * B * 3;
+    int* dst = c->stage_i;
+    int rc = whg_read_state_device(c, dx, du, dst, dtm);
+    if (rc) return rc;
+    WHG_CUDA(c, cudaMemcpyAsync(pos, dx, S * B * 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    WHG_CUDA(c, cudaMemcpyAsync(vel, du, S * B * 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (status)
+        WHG_CUDA(c, cudaMemcpyAsync(status, dst, S * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    if (t) WHG_CUDA(c, cudaMemcpyAsync(t, dtm, S * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    WHG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return WHG_OK;
+}
+
+int whg_energy_device(whg_ctx* c, double* E)
+{
+    if (!c) return WHG_EINVAL;
+    if (!c->initialized) return fail(c, WHG_ESTATE, "energy before whg_init");
+    if (!E) return fail(c, WHG_EINVAL, "null output array");
+    WhgOut o{};
+    o.E = E;
+    return launch_check(c, c->kern->energy(c->st, o, c->opt.newton_terms, c->opt.gr_mode, launch_cfg(c)),
+                        "energy kernel");
+}
+
+int whg_energy(whg_ctx* c, double* E)
+{
+    if (!c) return WHG_EINVAL;
+    if (!E) return fail(c, WHG_EINVAL, "null output array");
+    int rc = whg_energy_device(c, c->stage_d);
+    if (rc) return rc;
+    WHG_CUDA(c, cudaMemcpyAsync(E, c->stage_d, (size_t)c->S * sizeof(double), cudaMemcpyDeviceToHost,
+                                c->stream));
+    WHG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return WHG_OK;
+}
+
+int whg_get_raw(whg_ctx* c, double* Q, double* v, long long* nstep, int* status)
+{
+    if (!c) return WHG_EINVAL;
+    if (!c->initialized) return fail(c, WHG_ESTATE, "get_raw before whg_init");
+    if (!Q || !v || !nstep || !status) return fail(c, WHG_EINVAL, "null output array");
+    const size_t S = c->S, N = c->Nmax;
+    WhgOut o{};
+    o.rawQ = c->stage_d;
+    o.rawv = c->stage_d + S * N * 3;
+    o.rawn = c->stage_l;
+    o.status = c->stage_i;
+    int rc = launch_check(c, c->kern->raw(c->st, o, 0, launch_cfg(c)), "raw kernel");
+    if (rc) return rc;
+    WHG_CUDA(c, cudaMemcpyAsync(Q, o.rawQ, S * N * 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    WHG_CUDA(c, cudaMemcpyAsync(v, o.rawv, S * N * 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    WHG_CUDA(c, cudaMemcpyAsync(nstep, o.rawn, S * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+    WHG_CUDA(c, cudaMemcpyAsync(status, o.status, S * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    WHG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return WHG_OK;
+}
+
+int whg_set_raw(whg_ctx* c, const double* Q, const double* v, const long long* nstep,
+                const int* status)
+{
+    if (!c) return WHG_EINVAL;
+    if (!c->initialized) return fail(c, WHG_ESTATE, "set_raw before whg_init");
+    if (!Q || !v || !nstep || !status) return fail(c, WHG_EINVAL, "null input array");
+    const size_t S = c->S, N = c->Nmax;
+    for (size_t s = 0; s < S; ++s)
+        if (nstep[s] < 0) return fail(c, WHG_EINVAL, "nstep[%zu] < 0", s);
+    double* dQ = c->stage_d;
+    double* dv = dQ + S * N * 3;
+    WHG_CUDA(c, cudaMemcpyAsync(dQ, Q, S * N * 3 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    WHG_CUDA(c, cudaMemcpyAsync(dv, v, S * N * 3 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    WHG_CUDA(c, cudaMemcpyAsync(c->stage_l, nstep, S * sizeof(long long), cudaMemcpyHostToDevice, c->stream));
+    WHG_CUDA(c, cudaMemcpyAsync(c->stage_i, status, S * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    WhgOut o{};
+    o.inQ = dQ;
+    o.inv = dv;
+    o.inn = c->stage_l;
+    o.ins = c->stage_i;
+    int rc = launch_check(c, c->kern->raw(c->st, o, 1, launch_cfg(c)), "raw kernel");
+    if (rc) return rc;
+    WHG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return WHG_OK;
+}
+
+int whg_synchronize(whg_ctx* c)
+{
+    if (!c) return WHG_EINVAL;
+    WHG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return WHG_OK;
+}
+
+long long whg_launch_count(const whg_ctx* c) { return c ? c->launches : 0; }
+
+const char* whg_last_error(const whg_ctx* c) { return c ? c->err : g_create_err; }
+
+void whg_destroy(whg_ctx* c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->st.m);
+    cudaFree(c->stage_d);
+    delete c;
+}
+
+}  // extern "C"

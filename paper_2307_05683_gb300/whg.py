@@ -1,0 +1,306 @@
+"""Thin Python binding of libwhg (include/whg.h): argument marshalling only.
+
+Every function here has the name of the C function it calls and does no
+arithmetic of the integration path: all of it runs in the library's CUDA
+kernels.  Host-buffer calls take numpy arrays; *_device calls take CUDA torch
+tensors (PyTorch is used only for device memory and streams).  The library
+must have been built (paper_2307_05683_gb300.build.build()); if it is
+missing every call raises, there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+WHG_OK, WHG_EINVAL, WHG_ECUDA, WHG_ENOMEM, WHG_ESTATE = 0, -1, -2, -3, -4
+WHG_STATUS_NONFINITE, WHG_STATUS_HYPERBOLIC, WHG_STATUS_INVALID = 1, 2, 4
+WHG_MAX_PLANETS = 8
+
+
+class WhgError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"libwhg error {code}: {message}")
+        self.code = code
+
+
+class whg_options(ctypes.Structure):
+    _fields_ = [("gr_mode", ctypes.c_int), ("c_light", ctypes.c_double),
+                ("newton_terms", ctypes.c_int), ("lanes_per_system", ctypes.c_int),
+                ("block_size", ctypes.c_int), ("steps_per_launch", ctypes.c_longlong)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libwhg.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libwhg.so not found at {path}: build it with "
+                               "paper_2307_05683_gb300.build.build() (there is no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        P, D, I, L = (ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+        sig = {
+            "whg_default_options": (None, [ctypes.POINTER(whg_options)]),
+            "whg_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(whg_options), ctypes.c_void_p]),
+            "whg_set_stream": (ctypes.c_int, [P, ctypes.c_void_p]),
+            "whg_init": (ctypes.c_int, [P, D, D, D, I, D]),
+            "whg_init_device": (ctypes.c_int, [P, D, D, D, I, D]),
+            "whg_step": (ctypes.c_int, [P, ctypes.c_longlong]),
+            "whg_read_state": (ctypes.c_int, [P, D, D, I, D]),
+            "whg_read_state_device": (ctypes.c_int, [P, D, D, I, D]),
+            "whg_energy": (ctypes.c_int, [P, D]),
+            "whg_energy_device": (ctypes.c_int, [P, D]),
+            "whg_get_raw": (ctypes.c_int, [P, D, D, L, I]),
+            "whg_set_raw": (ctypes.c_int, [P, D, D, L, I]),
+            "whg_synchronize": (ctypes.c_int, [P]),
+            "whg_launch_count": (ctypes.c_longlong, [P]),
+            "whg_last_error": (ctypes.c_char_p, [P]),
+            "whg_destroy": (None, [P]),
+            "whg_measure_fp64_tflops": (ctypes.c_int, [ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+            "whg_test_special": (ctypes.c_int, [D, ctypes.c_int, D]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def exported_symbols() -> list[str]:
+    """Names of the C functions this binding expects the library to export."""
+    return ["whg_default_options", "whg_create", "whg_set_stream", "whg_init", "whg_init_device",
+            "whg_step", "whg_read_state", "whg_read_state_device", "whg_energy",
+            "whg_energy_device", "whg_get_raw", "whg_set_raw", "whg_synchronize",
+            "whg_launch_count", "whg_last_error", "whg_destroy", "whg_measure_fp64_tflops",
+            "whg_test_special"]
+
+
+def _check(ctx, rc: int) -> None:
+    if rc != WHG_OK:
+        msg = load().whg_last_error(ctx)
+        raise WhgError(rc, msg.decode() if msg else "")
+
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data
+
+
+def _dev(t, dtype_name: str):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous() or str(t.dtype) != dtype_name:
+        raise ValueError(f"expected a contiguous CUDA tensor of {dtype_name}")
+    return t.data_ptr()
+
+
+def current_stream():
+    """torch's current CUDA stream handle (or None)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------- calls --
+
+def whg_default_options() -> whg_options:
+    o = whg_options()
+    load().whg_default_options(ctypes.byref(o))
+    return o
+
+
+def whg_create(n_systems: int, max_planets: int, options: whg_options | None = None,
+               stream=None):
+    h = ctypes.c_void_p()
+    opt = ctypes.byref(options) if options is not None else None
+    rc = load().whg_create(ctypes.byref(h), int(n_systems), int(max_planets), opt,
+                           ctypes.c_void_p(stream) if stream else None)
+    _check(None, rc)
+    return h
+
+
+def whg_set_stream(ctx, stream) -> None:
+    _check(ctx, load().whg_set_stream(ctx, ctypes.c_void_p(stream) if stream else None))
+
+
+def whg_init(ctx, masses, pos, vel, n_planets, dt) -> None:
+    m, pm = _host(masses, np.float64)
+    x, px = _host(pos, np.float64)
+    u, pu = _host(vel, np.float64)
+    d, pd = _host(dt, np.float64)
+    if n_planets is not None:
+        n, pn = _host(n_planets, np.int32)
+    else:
+        pn = None
+    _check(ctx, load().whg_init(ctx, pm, px, pu, pn, pd))
+
+
+def whg_init_device(ctx, masses, pos, vel, n_planets, dt) -> None:
+    _check(ctx, load().whg_init_device(ctx, _dev(masses, "torch.float64"), _dev(pos, "torch.float64"),
+                                       _dev(vel, "torch.float64"), _dev(n_planets, "torch.int32"),
+                                       _dev(dt, "torch.float64")))
+
+
+def whg_step(ctx, n_steps: int) -> None:
+    _check(ctx, load().whg_step(ctx, int(n_steps)))
+
+
+def whg_read_state(ctx, pos: np.ndarray, vel: np.ndarray, status: np.ndarray | None = None,
+                   t: np.ndarray | None = None) -> None:
+    for a, dt in ((pos, np.float64), (vel, np.float64), (status, np.int32), (t, np.float64)):
+        if a is not None and (a.dtype != dt or not a.flags.c_contiguous):
+            raise ValueError("output arrays must be C-contiguous with the documented dtypes")
+    _check(ctx, load().whg_read_state(ctx, pos.ctypes.data, vel.ctypes.data,
+                                      status.ctypes.data if status is not None else None,
+                                      t.ctypes.data if t is not None else None))
+
+
+def whg_read_state_device(ctx, pos, vel, status=None, t=None) -> None:
+    _check(ctx, load().whg_read_state_device(ctx, _dev(pos, "torch.float64"), _dev(vel, "torch.float64"),
+                                             _dev(status, "torch.int32"), _dev(t, "torch.float64")))
+
+
+def whg_energy(ctx, E: np.ndarray) -> None:
+    if E.dtype != np.float64 or not E.flags.c_contiguous:
+        raise ValueError("E must be a contiguous float64 array")
+    _check(ctx, load().whg_energy(ctx, E.ctypes.data))
+
+
+def whg_energy_device(ctx, E) -> None:
+    _check(ctx, load().whg_energy_device(ctx, _dev(E, "torch.float64")))
+
+
+def whg_get_raw(ctx, Q: np.ndarray, v: np.ndarray, nstep: np.ndarray, status: np.ndarray) -> None:
+    _check(ctx, load().whg_get_raw(ctx, Q.ctypes.data, v.ctypes.data, nstep.ctypes.data,
+                                   status.ctypes.data))
+
+
+def whg_set_raw(ctx, Q, v, nstep, status) -> None:
+    Q, pq = _host(Q, np.float64)
+    v, pv = _host(v, np.float64)
+    n, pn = _host(nstep, np.int64)
+    s, ps = _host(status, np.int32)
+    _check(ctx, load().whg_set_raw(ctx, pq, pv, pn, ps))
+
+
+def whg_synchronize(ctx) -> None:
+    _check(ctx, load().whg_synchronize(ctx))
+
+
+def whg_launch_count(ctx) -> int:
+    return int(load().whg_launch_count(ctx))
+
+
+def whg_last_error(ctx=None) -> str:
+    msg = load().whg_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def whg_destroy(ctx) -> None:
+    load().whg_destroy(ctx)
+
+
+def whg_measure_fp64_tflops(seconds: float = 0.5) -> float:
+    out = ctypes.c_double()
+    _check(None, load().whg_measure_fp64_tflops(float(seconds), ctypes.byref(out)))
+    return out.value
+
+
+def whg_test_special(x, out) -> None:
+    _check(None, load().whg_test_special(_dev(x, "torch.float64"), int(x.numel()),
+                                         _dev(out, "torch.float64")))
+
+
+# ------------------------------------------------------------ convenience --
+
+class Integrator:
+    """One libwhg context: S systems of at most N planets (host-array API)."""
+
+    def __init__(self, n_systems: int, max_planets: int, gr_mode: int = 1, c_light: float | None = None,
+                 newton_terms: int = 8, lanes_per_system: int = 0, block_size: int = 0,
+                 steps_per_launch: int = 0, stream=None):
+        opt = whg_default_options()
+        opt.gr_mode = gr_mode
+        if c_light is not None:
+            opt.c_light = c_light
+        opt.newton_terms = newton_terms
+        opt.lanes_per_system = lanes_per_system
+        opt.block_size = block_size
+        opt.steps_per_launch = steps_per_launch
+        self.S, self.N = int(n_systems), int(max_planets)
+        self.stream = stream if stream is not None else current_stream()
+        self.ctx = whg_create(self.S, self.N, opt, self.stream)
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            whg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def init(self, ens) -> None:
+        whg_init(self.ctx, ens.masses, ens.pos, ens.vel, ens.n_planets, ens.dt)
+
+    def step(self, n: int) -> None:
+        whg_step(self.ctx, n)
+
+    def read_state(self):
+        pos = np.zeros((self.S, 1 + self.N, 3))
+        vel = np.zeros((self.S, 1 + self.N, 3))
+        st = np.zeros(self.S, np.int32)
+        t = np.zeros(self.S)
+        whg_read_state(self.ctx, pos, vel, st, t)
+        return pos, vel, st, t
+
+    def energy(self) -> np.ndarray:
+        E = np.zeros(self.S)
+        whg_energy(self.ctx, E)
+        return E
+
+    def get_raw(self):
+        Q = np.zeros((self.S, self.N, 3))
+        v = np.zeros((self.S, self.N, 3))
+        ns = np.zeros(self.S, np.int64)
+        st = np.zeros(self.S, np.int32)
+        whg_get_raw(self.ctx, Q, v, ns, st)
+        return Q, v, ns, st
+
+    def set_raw(self, Q, v, nstep, status) -> None:
+        whg_set_raw(self.ctx, Q, v, nstep, status)
+
+    def synchronize(self) -> None:
+        whg_synchronize(self.ctx)
+
+    @property
+    def launches(self) -> int:
+        return whg_launch_count(self.ctx)

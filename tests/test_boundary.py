@@ -1,0 +1,60 @@
+"""The C ABI: include/whg.h declarations, the built library's exports, and the
+Python binding's names.  CPU only (no CUDA calls are made)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "whg.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(whg_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2307_05683_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ["whg_create", "whg_init", "whg_step", "whg_read_state", "whg_energy",
+              "whg_get_raw", "whg_set_raw", "whg_last_error", "whg_destroy"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    out = subprocess.check_output(["nm", "-D", "--defined-only", lib_path], text=True)
+    exported = set(re.findall(r"\bT (whg_[a-z0-9_]+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    lib = ctypes.CDLL(lib_path)
+    for n in declared_functions():
+        assert getattr(lib, n) is not None
+
+
+def test_binding_covers_the_header(lib_path):
+    from paper_2307_05683_gb300 import whg
+    assert sorted(whg.exported_symbols()) == declared_functions()
+    for n in declared_functions():
+        assert callable(getattr(whg, n))
+
+
+def test_library_is_built_for_sm_103a(lib_path):
+    from paper_2307_05683_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.NVCC_FLAGS)
+
+
+def test_options_struct_layout(lib_path):
+    from paper_2307_05683_gb300 import whg
+    o = whg.whg_default_options()          # pure host function, no CUDA call
+    assert o.gr_mode == 1 and o.newton_terms == 8
+    assert o.c_light == pytest.approx(10065.32, rel=1e-5)
+    assert ctypes.sizeof(whg.whg_options) == 40

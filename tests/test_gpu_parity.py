@@ -1,0 +1,341 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances (the target the integrator is held to): after 1 step, 1e-12
+relative; after 1e4 steps, 1e-9 relative; "relative" per coordinate with each
+system's largest |coordinate| as the scale for inertial output, and each
+planet's own |Q_i|, |v_i| for the raw heliocentric state.  Run-to-run and
+launch-split results are compared bit for bit.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2307_05683_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+CORES = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def whg():
+    from paper_2307_05683_gb300 import build, whg as w
+    build.build()
+    w.load()
+    return w
+
+
+def gpu_run(whg, ens, n, chunks=None, **kw):
+    it = whg.Integrator(ens.n_systems, ens.max_planets, **kw)
+    it.init(ens)
+    for k in (chunks or [n]):
+        it.step(k)
+    out = it.read_state() + it.get_raw() + (it.energy(),)
+    it.close()
+    return out
+
+
+def oracle_run(orc, ens, n, gr_mode=1, newton_terms=8, c_light=None):
+    kw = dict(gr_mode=gr_mode, newton_terms=newton_terms)
+    if c_light is not None:
+        kw["c_light"] = c_light
+    o = orc.OracleEnsemble(ens.n_systems, ens.max_planets, **kw)
+    o.init(ens)
+    if n:
+        o.run_threads(n, CORES)
+    return o.read_state() + o.get_raw() + (o.energy(),)
+
+
+def assert_parity(g, o, tol, n_planets):
+    pos_g, vel_g, st_g, t_g, Q_g, v_g, ns_g, _, E_g = g
+    pos_o, vel_o, st_o, t_o, Q_o, v_o, ns_o, _, E_o = o
+    assert np.array_equal(st_g, st_o)
+    assert np.array_equal(ns_g, ns_o)
+    assert np.allclose(t_g, t_o, rtol=1e-15, atol=0)
+    sx = np.abs(pos_o).max(axis=(1, 2))[:, None, None]
+    su = np.abs(vel_o).max(axis=(1, 2))[:, None, None]
+    assert (np.abs(pos_g - pos_o) / sx).max() <= tol
+    assert (np.abs(vel_g - vel_o) / su).max() <= tol
+    live = np.arange(Q_o.shape[1])[None, :] < n_planets[:, None]
+    nq = np.linalg.norm(Q_o, axis=2)
+    nv = np.linalg.norm(v_o, axis=2)
+    eq = np.linalg.norm(Q_g - Q_o, axis=2)
+    ev = np.linalg.norm(v_g - v_o, axis=2)
+    assert (eq[live] / nq[live]).max() <= tol
+    assert (ev[live] / nv[live]).max() <= tol
+    assert np.all(Q_g[~live] == 0) and np.all(v_g[~live] == 0)
+    assert (np.abs(E_g - E_o) / np.abs(E_o)).max() <= max(tol, 1e-13)
+
+
+# ------------------------------------------------------ special functions --
+
+def test_own_rcp_rsqrt_against_cuda(whg):
+    import torch
+    rng = np.random.default_rng(0)
+    x = np.concatenate([10.0 ** rng.uniform(-300, 300, 200000),
+                        10.0 ** rng.uniform(-6, 6, 200000),
+                        1.0 + rng.uniform(-1e-9, 1e-9, 1000), [1.0, 2.0, 4.0, 0.5, 3.0]])
+    xt = torch.tensor(x, dtype=torch.float64, device="cuda")
+    out = torch.empty(4 * x.size, dtype=torch.float64, device="cuda")
+    whg.whg_test_special(xt, out)
+    r = out.cpu().numpy().reshape(4, -1)
+    ulp_rcp = np.spacing(np.abs(r[1]))
+    ulp_rsq = np.spacing(np.abs(r[3]))
+    # CUDA's 1/x is correctly rounded; rsqrt is within 1 ulp of exact.
+    assert (np.abs(r[0] - r[1]) / ulp_rcp).max() <= 1.0
+    assert (np.abs(r[2] - r[3]) / ulp_rsq).max() <= 2.0
+    assert np.mean(r[0] == r[1]) > 0.9
+    # and against the exact value (long double reference) for the planetary range
+    sel = (x > 1e-6) & (x < 1e6)
+    xl = x[sel].astype(np.longdouble)
+    exact_rsq = 1 / np.sqrt(xl)
+    err = np.abs(r[2][sel].astype(np.longdouble) - exact_rsq) / np.spacing(np.abs(r[3][sel]))
+    assert float(err.max()) <= 1.5
+
+
+# ------------------------------------------------------------- parity --
+
+@pytest.mark.parametrize("n,tol", [(1, 1e-12), (10000, 1e-9)])
+def test_two_planet_systems(whg, orc, n, tol):
+    """Two-planet systems (seeds 0..9), GR off: 1 step and the full 1e4 steps."""
+    ens = inputs.two_planet_system(0, 10)
+    g = gpu_run(whg, ens, n, gr_mode=0)
+    o = oracle_run(orc, ens, n, gr_mode=0)
+    assert_parity(g, o, tol, ens.n_planets)
+
+
+@pytest.mark.parametrize("gr_mode", [0, 1, 2])
+@pytest.mark.parametrize("n,tol", [(1, 1e-12), (100, 1e-11)])
+def test_solar_ensemble_short(whg, orc, gr_mode, n, tol):
+    ens = inputs.solar_ensemble(1, 96)
+    g = gpu_run(whg, ens, n, gr_mode=gr_mode)
+    o = oracle_run(orc, ens, n, gr_mode=gr_mode)
+    assert_parity(g, o, tol, ens.n_planets)
+
+
+def test_solar_ensemble_1e4_window(whg, orc):
+    """Solar-System-shaped ensemble, GR on, 1e4-step window (256 systems)."""
+    ens = inputs.solar_ensemble(2, 256)
+    g = gpu_run(whg, ens, 10000, gr_mode=1)
+    o = oracle_run(orc, ens, 10000, gr_mode=1)
+    assert_parity(g, o, 1e-9, ens.n_planets)
+
+
+def test_newton_terms_6(whg, orc):
+    ens = inputs.solar_ensemble(3, 64)
+    g = gpu_run(whg, ens, 500, gr_mode=1, newton_terms=6)
+    o = oracle_run(orc, ens, 500, gr_mode=1, newton_terms=6)
+    assert_parity(g, o, 1e-10, ens.n_planets)
+
+
+@pytest.mark.parametrize("lanes", [0, 8])
+def test_uneven_planet_counts(whg, orc, lanes):
+    """2..8 planets per system in one ensemble (padding lanes), and forcing
+    8 lanes per system."""
+    ens = inputs.compact_ensemble(5, 200)
+    g = gpu_run(whg, ens, 2000, gr_mode=1, lanes_per_system=lanes)
+    o = oracle_run(orc, ens, 2000, gr_mode=1)
+    assert_parity(g, o, 1e-10, ens.n_planets)
+
+
+@pytest.mark.parametrize("nmax", [1, 2, 3, 4, 5])
+def test_lanes_per_system_variants(whg, orc, nmax):
+    """G = 1, 2, 4, 4 (one padding lane), 8 (three padding lanes)."""
+    ens = inputs.compact_ensemble(6, 100)
+    ens = inputs.Ensemble(ens.masses[:, :1 + nmax].copy(), ens.pos[:, :1 + nmax].copy(),
+                          ens.vel[:, :1 + nmax].copy(), np.minimum(ens.n_planets, nmax), ens.dt)
+    ens = inputs._assemble(1.0, ens.masses[:, 1:], ens.pos[:, 1:] - ens.pos[:, :1],
+                           ens.vel[:, 1:] - ens.vel[:, :1], ens.n_planets, ens.dt, "")
+    g = gpu_run(whg, ens, 1000, gr_mode=1)
+    o = oracle_run(orc, ens, 1000, gr_mode=1)
+    assert_parity(g, o, 1e-10, ens.n_planets)
+
+
+def test_massless_test_particles(whg, orc):
+    """Massless planets (drift-only problem of the paper's Fig. 1)."""
+    ens = inputs.test_particle(np.linspace(0.3, 2.0, 40), np.linspace(0.0, 0.6, 40),
+                               np.linspace(0, 6, 40))
+    g = gpu_run(whg, ens, 3000, gr_mode=0)
+    o = oracle_run(orc, ens, 3000, gr_mode=0)
+    assert_parity(g, o, 1e-10, ens.n_planets)
+
+
+# --------------------------------------------------- determinism, resume --
+
+def test_bitwise_run_to_run_and_launch_split(whg):
+    ens = inputs.solar_ensemble(4, 300)
+    a = gpu_run(whg, ens, 2000, gr_mode=1)
+    b = gpu_run(whg, ens, 2000, gr_mode=1)
+    c = gpu_run(whg, ens, 2000, chunks=[1, 999, 1000], gr_mode=1)
+    d = gpu_run(whg, ens, 2000, gr_mode=1, steps_per_launch=7)
+    for x in (b, c, d):
+        for u, v in zip(a, x):
+            assert np.array_equal(u, v)
+
+
+def test_keep_unsynchronized_reads_do_not_change_bits(whg):
+    ens = inputs.solar_ensemble(5, 64)
+    it = whg.Integrator(64, 8)
+    it.init(ens)
+    for _ in range(4):
+        it.step(250)
+        it.read_state()
+        it.energy()
+    raw_a = it.get_raw()
+    it2 = whg.Integrator(64, 8)
+    it2.init(ens)
+    it2.step(1000)
+    for u, v in zip(raw_a, it2.get_raw()):
+        assert np.array_equal(u, v)
+    # checkpoint into a fresh context and resume bit-identically
+    it3 = whg.Integrator(64, 8)
+    it3.init(ens)
+    it3.set_raw(*raw_a)
+    it.step(333)
+    it3.step(333)
+    for u, v in zip(it.get_raw(), it3.get_raw()):
+        assert np.array_equal(u, v)
+
+
+def test_device_pointer_api_matches_host_api(whg):
+    import torch
+    ens = inputs.solar_ensemble(6, 50)
+    it = whg.Integrator(50, 8)
+    it.init(ens)
+    it.step(123)
+    ref = it.read_state()
+    dev = whg.Integrator(50, 8)
+    t = lambda a, dt=torch.float64: torch.tensor(a, dtype=dt, device="cuda")
+    whg.whg_init_device(dev.ctx, t(ens.masses), t(ens.pos), t(ens.vel),
+                        t(ens.n_planets, torch.int32), t(ens.dt))
+    dev.step(123)
+    pos = torch.empty((50, 9, 3), dtype=torch.float64, device="cuda")
+    vel = torch.empty_like(pos)
+    st = torch.empty(50, dtype=torch.int32, device="cuda")
+    tt = torch.empty(50, dtype=torch.float64, device="cuda")
+    whg.whg_read_state_device(dev.ctx, pos, vel, st, tt)
+    E = torch.empty(50, dtype=torch.float64, device="cuda")
+    whg.whg_energy_device(dev.ctx, E)
+    torch.cuda.synchronize()
+    assert np.array_equal(pos.cpu().numpy(), ref[0])
+    assert np.array_equal(vel.cpu().numpy(), ref[1])
+    assert np.array_equal(st.cpu().numpy(), ref[2])
+    assert np.array_equal(E.cpu().numpy(), it.energy())
+
+
+# ------------------------------------------------------ edge cases, status --
+
+def test_status_freeze_matches_oracle(whg, orc):
+    """An unbound planet (HYPERBOLIC) and a coincident pair (NONFINITE) freeze
+    their systems at the same step as the oracle; the others run on."""
+    ens = inputs.two_planet_system(3, 4)
+    ens.vel[1, 2] *= 3.0                       # unbound outer planet
+    ens.pos[2, 2] = ens.pos[2, 1]
+    ens.vel[2, 2] = ens.vel[2, 1]              # same position and velocity
+    g = gpu_run(whg, ens, 50, gr_mode=0)
+    o = oracle_run(orc, ens, 50, gr_mode=0)
+    assert list(g[2]) == [0, 2, 1, 0]
+    assert_parity(g, o, 1e-12, ens.n_planets)
+
+
+def test_invalid_inputs_are_rejected(whg):
+    ens = inputs.two_planet_system(0, 3)
+    it = whg.Integrator(3, 2)
+    with pytest.raises(whg.WhgError) as e:
+        it.step(1)
+    assert e.value.code == whg.WHG_ESTATE
+    for bad in ("dt", "mass", "nan", "nplan", "onstar"):
+        e2 = inputs.Ensemble(ens.masses.copy(), ens.pos.copy(), ens.vel.copy(),
+                             ens.n_planets.copy(), ens.dt.copy())
+        if bad == "dt":
+            e2.dt[1] = 0.0
+        elif bad == "mass":
+            e2.masses[1, 2] = -1e-6
+        elif bad == "nan":
+            e2.vel[2, 1, 0] = np.nan
+        elif bad == "nplan":
+            e2.n_planets[0] = 3
+        else:
+            e2.pos[0, 1] = e2.pos[0, 0]
+        with pytest.raises(whg.WhgError) as e:
+            it.init(e2)
+        assert e.value.code == whg.WHG_EINVAL
+        assert "system" in whg.whg_last_error(it.ctx)
+    with pytest.raises(whg.WhgError):
+        whg.whg_create(0, 2)
+    with pytest.raises(whg.WhgError):
+        whg.whg_create(4, 9)
+
+
+def test_device_init_marks_invalid_systems(whg):
+    import torch
+    ens = inputs.two_planet_system(1, 4)
+    ens.dt[2] = -1.0
+    it = whg.Integrator(4, 2)
+    t = lambda a, dt=torch.float64: torch.tensor(a, dtype=dt, device="cuda")
+    whg.whg_init_device(it.ctx, t(ens.masses), t(ens.pos), t(ens.vel), t(ens.n_planets, torch.int32),
+                        t(ens.dt))
+    it.step(10)
+    _, _, st, tt = it.read_state()
+    assert list(st) == [0, 0, whg.WHG_STATUS_INVALID, 0]
+    assert tt[2] == 0.0 and tt[0] > 0
+
+
+def test_zero_steps_and_single_system(whg, orc):
+    ens = inputs.two_planet_system(7, 1)
+    g = gpu_run(whg, ens, 0, gr_mode=0)
+    assert np.allclose(g[0], ens.pos, rtol=0, atol=1e-15)
+    o = oracle_run(orc, ens, 0, gr_mode=0)
+    assert_parity(g, o, 1e-14, ens.n_planets)
+
+
+@pytest.mark.parametrize("S", [1, 31, 33, 4097])
+def test_ragged_system_counts(whg, orc, S):
+    """System counts that leave a partial block / warp (padding systems)."""
+    ens = inputs.solar_ensemble(8, S)
+    g = gpu_run(whg, ens, 20, gr_mode=1)
+    o = oracle_run(orc, ens, 20, gr_mode=1)
+    assert_parity(g, o, 1e-12, ens.n_planets)
+
+
+def test_full_size_ensemble_sampled(whg, orc):
+    """2^20 systems (the largest sweep size), 20 steps; 512 sampled systems
+    checked against the oracle one by one."""
+    S = 1 << 20
+    ens = inputs.solar_ensemble(9, 4096).tile(S)
+    rng = np.random.default_rng(1)
+    idx = np.sort(rng.choice(S, 512, replace=False))
+    it = whg.Integrator(S, 8)
+    it.init(ens)
+    it.step(20)
+    pos, vel, st, t = it.read_state()
+    it.close()
+    sub = ens.subset(idx)
+    o = orc.OracleEnsemble(512, 8, gr_mode=1)
+    o.init(sub)
+    o.run_threads(20, CORES)
+    po, vo, so, to = o.read_state()
+    assert np.array_equal(st[idx], so)
+    sx = np.abs(po).max(axis=(1, 2))[:, None, None]
+    assert (np.abs(pos[idx] - po) / sx).max() <= 1e-12
+    # systems that are copies of one another stay bitwise identical
+    assert np.array_equal(pos[5], pos[5 + 4096])
+
+
+def test_energy_error_statistics_match(whg, orc):
+    """Relative energy errors over a 2e4-step run: same per-system values
+    (to 1e-12 absolute) and the same distribution."""
+    ens = inputs.solar_ensemble(10, 128)
+    it = whg.Integrator(128, 8)
+    it.init(ens)
+    E0 = it.energy()
+    it.step(20000)
+    dEg = it.energy() / E0 - 1
+    o = orc.OracleEnsemble(128, 8, gr_mode=1)
+    o.init(ens)
+    E0o = o.energy()
+    o.run_threads(20000, CORES)
+    dEo = o.energy() / E0o - 1
+    assert np.abs(dEg - dEo).max() < 1e-12
+    assert np.abs(dEg).max() < 1e-6
