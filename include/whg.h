@@ -151,6 +151,39 @@ const char* whg_last_error(const whg_ctx* ctx);
 /* Free all resources of ctx (NULL is a no-op).  Synchronizes its stream. */
 void whg_destroy(whg_ctx* ctx);
 
+/* ---- allocation-free variant -------------------------------------------- */
+
+/* The paper has no counterpart of this call: it exists for callers that
+ * cannot allocate device memory, such as frameworks that reserve the GPU's
+ * memory up front and only hand out buffers from their own pool, host
+ * programs or plugins that forbid device allocation once running, and loops
+ * that cannot afford cudaMalloc's implicit device-wide synchronization.
+ *
+ * Does what whg_create + whg_init_device + whg_step(n_steps) +
+ * whg_read_state_device would do, with the same kernels and results, but
+ * calls no cudaMalloc, cudaFree or other allocating routine: the working state
+ * lives in one fixed array of about 9 MiB in the library's device memory,
+ * which every GPU that loads the library holds until the process exits.
+ * All array pointers are DEVICE pointers with the layouts above (n_planets,
+ * status_out and t_out may be NULL); work is issued on cuda_stream (NULL =
+ * legacy default stream) and the call returns after enqueueing it.
+ *
+ * Limit: n_systems x lanes per system (padded up to whole CUDA blocks) must
+ * not exceed WHG_NOALLOC_MAX_LANES, e.g. 8192 systems of 5..8 planets with the
+ * default 32-thread blocks; larger requests fail with WHG_EINVAL.
+ * The first call on each device looks up the array's device address; make
+ * that first call before any stream capture.
+ * Every call reuses the same array and leaves its contents behind; each call
+ * rewrites everything it reads before reading it.  Calls whose GPU work
+ * overlaps (other streams, other host threads) race on the array: order them.
+ * Errors are reported by the return code and whg_last_error(NULL). */
+#define WHG_NOALLOC_MAX_LANES 65536
+int whg_integrate_noalloc(int n_systems, int max_planets, const whg_options* opt,
+                          const double* masses, const double* pos, const double* vel,
+                          const int* n_planets, const double* dt, long long n_steps,
+                          double* pos_out, double* vel_out, int* status_out, double* t_out,
+                          void* cuda_stream);
+
 /* ---- diagnostics (not part of the integration path) -------------------- */
 
 /* FP64 pipe throughput: runs a dependent-FMA loop on every SM of the current

@@ -115,6 +115,8 @@ int launch_check(whg_ctx* c, cudaError_t e, const char* what)
 
 }  // namespace
 
+void whg_record_error(const char* msg) { snprintf(g_create_err, sizeof g_create_err, "%s", msg); }
+
 extern "C" {
 
 void whg_default_options(whg_options* opt)

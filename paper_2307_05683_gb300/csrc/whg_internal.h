@@ -74,3 +74,6 @@ extern const WhgKernels whg_kernels_g4;
 extern const WhgKernels whg_kernels_g8;
 
 #define WHG_MAX_BLOCK 256
+
+// Record the message returned by whg_last_error(NULL) for calls without a context.
+void whg_record_error(const char* msg);

@@ -1,0 +1,168 @@
+// whg_noalloc.cu -- whg_integrate_noalloc: init + n steps + synchronized read
+// of an ensemble in one call that allocates no memory.
+//
+// For callers that cannot allocate device memory themselves or let a library
+// do it: frameworks that reserve the GPU's memory up front and only hand out
+// buffers from their own pool, host applications or plugins whose policy
+// forbids device allocation once they are running, and loops that cannot pay
+// cudaMalloc's implicit device-wide synchronization.  The caller passes device
+// inputs and outputs; the working state (democratic heliocentric coordinates
+// between the init, step and read kernels) lives in the fixed array below.
+#include <cstdio>
+#include <mutex>
+
+#include "whg_internal.h"
+
+namespace {
+
+// Layout of the working state for at most WHG_NOALLOC_MAX_LANES lanes
+// (systems x lanes per system, after padding to whole blocks): 7 lane arrays,
+// 9 per-system doubles, one per-system int64 and two per-system ints.
+constexpr size_t kLanes = WHG_NOALLOC_MAX_LANES;
+constexpr size_t kSystems = WHG_NOALLOC_MAX_LANES;   // at least one lane per system
+constexpr size_t kBytes = (7 * kLanes + 9 * kSystems) * sizeof(double) + kSystems * sizeof(long long) +
+                          2 * kSystems * sizeof(int);
+
+// Device-side scratch.  In host code this name is only a host stand-in: its
+// device address comes from cudaGetSymbolAddress (per device, below).
+static __device__ __align__(256) unsigned char g_scratch[kBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mutex;
+void* g_scratch_addr[kMaxDevices] = {};
+
+int noalloc_fail(int code, const char* fmt, const char* detail)
+{
+    char msg[256];
+    snprintf(msg, sizeof msg, fmt, detail);
+    whg_record_error(msg);
+    return code;
+}
+
+// Device address of g_scratch on the current device, looked up once per device.
+int scratch_address(void** out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return noalloc_fail(WHG_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(WHG_EINVAL, "device index %s not supported", "out of range");
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess || !p)
+            return noalloc_fail(WHG_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return WHG_OK;
+}
+
+const WhgKernels* kernels_for_lanes(int G)
+{
+    switch (G) {
+    case 1: return &whg_kernels_g1;
+    case 2: return &whg_kernels_g2;
+    case 4: return &whg_kernels_g4;
+    case 8: return &whg_kernels_g8;
+    default: return nullptr;
+    }
+}
+
+}  // namespace
+
+extern "C" int whg_integrate_noalloc(int n_systems, int max_planets, const whg_options* opt_in,
+                                     const double* masses, const double* pos, const double* vel,
+                                     const int* n_planets, const double* dt, long long n_steps,
+                                     double* pos_out, double* vel_out, int* status_out, double* t_out,
+                                     void* cuda_stream)
+{
+    whg_options opt;
+    whg_default_options(&opt);
+    if (opt_in) opt = *opt_in;
+    if (n_systems < 1 || max_planets < 1 || max_planets > WHG_MAX_PLANETS)
+        return noalloc_fail(WHG_EINVAL, "whg_integrate_noalloc: %s", "need n_systems >= 1 and max_planets in 1..8");
+    if (!masses || !pos || !vel || !dt || !pos_out || !vel_out)
+        return noalloc_fail(WHG_EINVAL, "whg_integrate_noalloc: %s", "null input or output array");
+    if (n_steps < 0) return noalloc_fail(WHG_EINVAL, "whg_integrate_noalloc: %s", "n_steps must be >= 0");
+    if (opt.gr_mode < 0 || opt.gr_mode > 2 || (opt.newton_terms != 6 && opt.newton_terms != 8) ||
+        (opt.gr_mode && !(opt.c_light > 0.0)) || opt.steps_per_launch < 0)
+        return noalloc_fail(WHG_EINVAL, "whg_integrate_noalloc: %s", "invalid options");
+    int G = opt.lanes_per_system;
+    if (G == 0) {
+        G = 1;
+        while (G < max_planets) G <<= 1;
+    }
+    const WhgKernels* kern = kernels_for_lanes(G);
+    if (!kern || G < max_planets)
+        return noalloc_fail(WHG_EINVAL, "whg_integrate_noalloc: %s", "lanes_per_system must be 1, 2, 4 or 8 and >= max_planets");
+    const int block = opt.block_size ? opt.block_size : 32;
+    if (block < 32 || block > WHG_MAX_BLOCK || block % 32)
+        return noalloc_fail(WHG_EINVAL, "whg_integrate_noalloc: %s", "block_size must be a multiple of 32 in 32..256");
+    const long long per_block = block / G;
+    const long long S_pad = ((long long)n_systems + per_block - 1) / per_block * per_block;
+    if (S_pad * G > (long long)kLanes) {
+        char why[160];
+        snprintf(why, sizeof why, "%d systems x %d lanes exceed the fixed scratch of %d lanes",
+                 n_systems, G, WHG_NOALLOC_MAX_LANES);
+        return noalloc_fail(WHG_EINVAL, "whg_integrate_noalloc: %s", why);
+    }
+
+    void* base = nullptr;
+    int rc = scratch_address(&base);
+    if (rc) return rc;
+
+    // Carve the state out of the scratch array (same layout as a context).
+    const size_t L = (size_t)S_pad * G, P = (size_t)S_pad;
+    WhgState st;
+    double* d = (double*)base;
+    st.m = d; d += L;
+    st.qx = d; d += L;
+    st.qy = d; d += L;
+    st.qz = d; d += L;
+    st.vx = d; d += L;
+    st.vy = d; d += L;
+    st.vz = d; d += L;
+    st.m0 = d; d += P;
+    st.dt = d; d += P;
+    st.M = d; d += P;
+    st.xcm = d; d += 3 * P;
+    st.vcm = d; d += 3 * P;
+    long long* ll = (long long*)d;
+    st.nstep = ll; ll += P;
+    int* ip = (int*)ll;
+    st.nplan = ip; ip += P;
+    st.status = ip;
+    st.S = n_systems;
+    st.S_pad = (int)S_pad;
+    st.Nmax = max_planets;
+    st.c_light = opt.c_light;
+
+    WhgLaunch l;
+    l.block = block;
+    l.grid = (int)(L / block);
+    l.stream = (cudaStream_t)cuda_stream;
+
+    // The init kernel writes every lane and per-system field read later
+    // (status and step counters start at zero), so stale contents left by an
+    // earlier call are never read.
+    WhgIn in{masses, pos, vel, n_planets, dt};
+    cudaError_t e = kern->init(st, in, l);
+    if (e != cudaSuccess) return noalloc_fail(WHG_ECUDA, "init kernel: %s", cudaGetErrorString(e));
+    long long chunk = opt.steps_per_launch > 0 ? opt.steps_per_launch : 50000000LL / (long long)S_pad;
+    if (chunk < 1) chunk = 1;
+    for (long long left = n_steps; left > 0;) {
+        const long long k = left < chunk ? left : chunk;
+        e = kern->step(st, k, opt.newton_terms, opt.gr_mode, l);
+        if (e != cudaSuccess) return noalloc_fail(WHG_ECUDA, "step kernel: %s", cudaGetErrorString(e));
+        left -= k;
+    }
+    WhgOut o{};
+    o.pos = pos_out;
+    o.vel = vel_out;
+    o.status = status_out;
+    o.t = t_out;
+    e = kern->read(st, o, opt.newton_terms, l);
+    if (e != cudaSuccess) return noalloc_fail(WHG_ECUDA, "read kernel: %s", cudaGetErrorString(e));
+    return WHG_OK;
+}

@@ -73,6 +73,9 @@ def load():
             "whg_destroy": (None, [P]),
             "whg_measure_fp64_tflops": (ctypes.c_int, [ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
             "whg_test_special": (ctypes.c_int, [D, ctypes.c_int, D]),
+            "whg_integrate_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int,
+                                                     ctypes.POINTER(whg_options), D, D, D, I, D,
+                                                     ctypes.c_longlong, D, D, I, D, ctypes.c_void_p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -88,7 +91,7 @@ def exported_symbols() -> list[str]:
             "whg_step", "whg_read_state", "whg_read_state_device", "whg_energy",
             "whg_energy_device", "whg_get_raw", "whg_set_raw", "whg_synchronize",
             "whg_launch_count", "whg_last_error", "whg_destroy", "whg_measure_fp64_tflops",
-            "whg_test_special"]
+            "whg_test_special", "whg_integrate_noalloc"]
 
 
 def _check(ctx, rc: int) -> None:
@@ -229,6 +232,23 @@ def whg_measure_fp64_tflops(seconds: float = 0.5) -> float:
 def whg_test_special(x, out) -> None:
     _check(None, load().whg_test_special(_dev(x, "torch.float64"), int(x.numel()),
                                          _dev(out, "torch.float64")))
+
+
+WHG_NOALLOC_MAX_LANES = 65536
+
+
+def whg_integrate_noalloc(n_systems: int, max_planets: int, options: whg_options | None,
+                          masses, pos, vel, n_planets, dt, n_steps: int,
+                          pos_out, vel_out, status_out=None, t_out=None, stream=None) -> None:
+    """Allocation-free init + step + read on CUDA tensors (see include/whg.h)."""
+    opt = ctypes.byref(options) if options is not None else None
+    rc = load().whg_integrate_noalloc(
+        int(n_systems), int(max_planets), opt, _dev(masses, "torch.float64"), _dev(pos, "torch.float64"),
+        _dev(vel, "torch.float64"), _dev(n_planets, "torch.int32"), _dev(dt, "torch.float64"),
+        int(n_steps), _dev(pos_out, "torch.float64"), _dev(vel_out, "torch.float64"),
+        _dev(status_out, "torch.int32"), _dev(t_out, "torch.float64"),
+        ctypes.c_void_p(stream) if stream else None)
+    _check(None, rc)
 
 
 # ------------------------------------------------------------ convenience --
