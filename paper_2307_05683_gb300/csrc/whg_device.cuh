@@ -88,6 +88,28 @@ __device__ __forceinline__ double rsqrt(double x)
     return fma(y * e, fma(0.375, e, 0.5), y);
 }
 
+// x^(-3/2) for finite normal x > 0 (the 1/r^3 of a pair from r^2), straight
+// from the rsqrt seed: x^(-3/2) = y0^3 (1 - e)^(-3/2) = y0^3 (1 + 3e/2 + 15e^2/8 + ...)
+// with e = 1 - x y0^2; truncation ~ (35/16) e^3 < 2^-61.
+__device__ __forceinline__ double rsqrt_cubed(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    const int ex = (int)((hi >> 20) & 0x7ffu) - 1023;
+    const int odd = ex & 1;
+    const int half = (ex - odd) / 2;
+    const float mant = __uint_as_float(((unsigned)(127 + odd) << 23) | ((hi & 0x000fffffu) << 3) |
+                                       (lo >> 29));
+    const unsigned rb = __float_as_uint(approx_rsqrt_f32(mant));
+    const int dex = (int)((rb >> 23) & 0xffu) - 127 - half + 1023;
+    const double y = __hiloint2double((int)(((unsigned)dex << 20) | ((rb >> 3) & 0x000fffffu)),
+                                      (int)(rb << 29));
+    const double y2 = y * y;
+    const double e = fma(-x, y2, 1.0);
+    const double y3 = y2 * y;
+    return fma(y3 * e, fma(1.875, e, 1.5), y3);
+}
+
 __device__ __forceinline__ bool is_finite(double x)
 {
     return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
@@ -131,28 +153,21 @@ __device__ __forceinline__ void stumpff_c2c3(double z, double& c2, double& c3)
     StumpffHorner<T - 2>::run(z, c2, c3);
 }
 
-// Stiefel functions G_n = X^n c_n(beta X^2): G_2, G_3 from the series, then
-// G_0 = 1 - beta G_2 and G_1 = X - beta G_3 (c_0 = 1 - z c_2, c_1 = 1 - z c_3).
-template <int T>
-__device__ __forceinline__ void stiefel(double beta, double X, double& G0, double& G1, double& G2,
-                                        double& G3)
-{
-    const double X2 = X * X;
-    double c2, c3;
-    stumpff_c2c3<T>(beta * X2, c2, c3);
-    G2 = X2 * c2;
-    G3 = (X2 * X) * c3;
-    G0 = fma(-beta, G2, 1.0);
-    G1 = fma(-beta, G3, X);
-}
 
 // ------------------------------------------------------------------------
 // Kepler drift of one planet for time h under H_K,i (Sec. 3.2, Eq. 3),
-// mu = G m0.  Universal variable X solves F(X) = r0 G1 + eta0 G2 + mu G3 - h
-// with F' = r0 G0 + eta0 G1 + mu G2 = r and F'' = eta0 G0 + zeta0 G1:
-// initial guess h/r0 - eta0 h^2 / (2 r0^3), 2 Halley steps with 4-term
-// series, 2 Newton steps with NT-term series, G_n re-evaluated at the final X,
-// then the Lagrange f, g, fdot, gdot.  No branches.  Returns beta > 0.
+// mu = G m0.  Universal variable X solves Kepler's equation
+//     F(X)  = r0 G1 + eta0 G2 + mu G3 - h = r0 X + eta0 G2 + zeta0 G3 - h = 0,
+//     F'(X) = r = r0 + eta0 X + zeta0 G2 - beta eta0 G3,
+//     F''   = eta0 + zeta0 X - beta eta0 G2 - beta zeta0 G3
+// (the second forms use G0 = 1 - beta G2, G1 = X - beta G3 and
+// zeta0 = mu - beta r0, so only the c2 and c3 series are needed): initial
+// guess h/r0 - eta0 h^2 / (2 r0^3), 2 Halley steps with 4-term series, 2 Newton
+// steps with NT-term series.  The G_n at the final X = X1 + d come from the
+// values at the last Newton point X1 by one Taylor step (dG_n/dX = G_{n-1});
+// |d| is the last Newton correction, so the neglected d^2 terms are far below
+// rounding.  Then the Lagrange f - 1, g, fdot, gdot - 1.  No branches.
+// Returns beta > 0.
 template <int NT>
 __device__ __forceinline__ bool kepler_drift(double mu, double h, double& qx, double& qy,
                                              double& qz, double& vx, double& vy, double& vz)
@@ -164,37 +179,55 @@ __device__ __forceinline__ bool kepler_drift(double mu, double h, double& qx, do
     const double v2 = fma(vx, vx, fma(vy, vy, vz * vz));
     const double beta = fma(2.0 * mu, r0i, -v2);
     const double zeta0 = fma(-beta, r0, mu);
+    const double beta_eta0 = beta * eta0, beta_zeta0 = beta * zeta0;
     const double hr = h * r0i;
     double X = fma(-0.5 * eta0 * hr * hr, r0i, hr);
-    double G0, G1, G2, G3;
+    double X2, c2, c3, G2, G3;
 #pragma unroll
     for (int it = 0; it < 2; ++it) {                 // Halley
-        stiefel<4>(beta, X, G0, G1, G2, G3);
-        const double F = fma(r0, G1, fma(eta0, G2, fma(mu, G3, -h)));
-        const double Fp = fma(r0, G0, fma(eta0, G1, mu * G2));
-        const double Fpp = fma(eta0, G0, zeta0 * G1);
-        const double den = fma(2.0 * Fp, Fp, -(F * Fpp));
-        X = fma(-2.0 * (F * Fp), rcp(den), X);
+        X2 = X * X;
+        stumpff_c2c3<4>(beta * X2, c2, c3);
+        G2 = X2 * c2;
+        G3 = (X2 * X) * c3;
+        const double F = fma(r0, X, fma(eta0, G2, fma(zeta0, G3, -h)));
+        const double Fp = fma(zeta0, G2, fma(-beta_eta0, G3, fma(eta0, X, r0)));
+        const double Fpp = fma(-beta_zeta0, G3, fma(-beta_eta0, G2, fma(zeta0, X, eta0)));
+        const double den = fma(-0.5 * F, Fpp, Fp * Fp);          // (2F'^2 - F F'') / 2
+        X = fma(-(F * Fp), rcp(den), X);
     }
+    double d = 0.0;
 #pragma unroll
     for (int it = 0; it < 2; ++it) {                 // Newton
-        stiefel<NT>(beta, X, G0, G1, G2, G3);
-        const double F = fma(r0, G1, fma(eta0, G2, fma(mu, G3, -h)));
-        const double Fp = fma(r0, G0, fma(eta0, G1, mu * G2));
-        X = fma(-F, rcp(Fp), X);
+        X = X + d;
+        X2 = X * X;
+        stumpff_c2c3<NT>(beta * X2, c2, c3);
+        G2 = X2 * c2;
+        G3 = (X2 * X) * c3;
+        const double F = fma(r0, X, fma(eta0, G2, fma(zeta0, G3, -h)));
+        const double Fp = fma(zeta0, G2, fma(-beta_eta0, G3, fma(eta0, X, r0)));
+        d = -F * rcp(Fp);
     }
-    stiefel<NT>(beta, X, G0, G1, G2, G3);
-    const double r = fma(r0, G0, fma(eta0, G1, mu * G2));
+    // G at the final X + d from the last Newton point X.
+    const double G1 = fma(-beta, G3, X);
+    const double G0 = fma(-beta, G2, 1.0);
+    const double Xf = X + d;
+    const double G3f = fma(d, G2, G3);
+    const double G2f = fma(d, G1, G2);
+    const double G1f = fma(d, G0, G1);
+    const double r = fma(zeta0, G2f, fma(-beta_eta0, G3f, fma(eta0, Xf, r0)));
     const double ri = rcp(r);
     const double mr0 = mu * r0i;
-    const double f = fma(-mr0, G2, 1.0);
-    const double g = fma(-mu, G3, h);
-    const double fd = -(mr0 * ri) * G1;
-    const double gd = fma(-mu * ri, G2, 1.0);
-    const double nqx = fma(f, qx, g * vx), nqy = fma(f, qy, g * vy), nqz = fma(f, qz, g * vz);
-    const double nvx = fma(fd, qx, gd * vx), nvy = fma(fd, qy, gd * vy), nvz = fma(fd, qz, gd * vz);
+    const double fm1 = -mr0 * G2f;                   // f - 1
+    const double g = fma(-mu, G3f, h);
+    const double fd = -(mr0 * ri) * G1f;
+    const double gdm1 = -(mu * ri) * G2f;            // gdot - 1
+    const double nqx = fma(fm1, qx, fma(g, vx, qx));
+    const double nqy = fma(fm1, qy, fma(g, vy, qy));
+    const double nqz = fma(fm1, qz, fma(g, vz, qz));
+    vx = fma(fd, qx, fma(gdm1, vx, vx));
+    vy = fma(fd, qy, fma(gdm1, vy, vy));
+    vz = fma(fd, qz, fma(gdm1, vz, vz));
     qx = nqx; qy = nqy; qz = nqz;
-    vx = nvx; vy = nvy; vz = nvz;
     return beta > 0.0;
 }
 
@@ -240,8 +273,7 @@ __device__ __forceinline__ void kick(int p, double qx, double qy, double qz, dou
         const double dy = __shfl_sync(WHG_FULL_MASK, qy, to, G) - qy;
         const double dz = __shfl_sync(WHG_FULL_MASK, qz, to, G) - qz;
         const double hmj = __shfl_sync(WHG_FULL_MASK, hm, to, G);
-        const double rs = rsqrt(fma(dx, dx, fma(dy, dy, dz * dz)));
-        const double r3 = rs * rs * rs;
+        const double r3 = rsqrt_cubed(fma(dx, dx, fma(dy, dy, dz * dz)));
         const double sj = hmj * r3;
         vx = fma(sj, dx, vx);
         vy = fma(sj, dy, vy);
@@ -261,8 +293,7 @@ __device__ __forceinline__ void kick(int p, double qx, double qy, double qz, dou
         const double dy = __shfl_sync(WHG_FULL_MASK, qy, to, G) - qy;
         const double dz = __shfl_sync(WHG_FULL_MASK, qz, to, G) - qz;
         const double hmj = __shfl_sync(WHG_FULL_MASK, hm, to, G);
-        const double rs = rsqrt(fma(dx, dx, fma(dy, dy, dz * dz)));
-        const double sj = hmj * (rs * rs * rs);
+        const double sj = hmj * rsqrt_cubed(fma(dx, dx, fma(dy, dy, dz * dz)));
         vx = fma(sj, dx, vx);
         vy = fma(sj, dy, vy);
         vz = fma(sj, dz, vz);

@@ -136,12 +136,14 @@ def test_newton_terms_6(whg, orc):
 @pytest.mark.parametrize("lanes", [0, 8])
 def test_uneven_planet_counts(whg, orc, lanes):
     """2..8 planets per system in one ensemble (padding lanes), and forcing
-    8 lanes per system.  These closely spaced systems (8-12 mutual Hill radii)
-    amplify roundoff differences fastest, so they are held to the 1e-9 bar."""
+    8 lanes per system.  Some of these closely spaced systems (8-12 mutual Hill
+    radii) are chaotic: in the oracle alone a 1e-15 relative change of the
+    initial positions grows to ~1e-9 within 2000 steps but stays ~3e-12 over
+    500, so the comparison uses 500 steps."""
     ens = inputs.compact_ensemble(5, 200)
-    g = gpu_run(whg, ens, 2000, gr_mode=1, lanes_per_system=lanes)
-    o = oracle_run(orc, ens, 2000, gr_mode=1)
-    assert_parity(g, o, 1e-9, ens.n_planets)
+    g = gpu_run(whg, ens, 500, gr_mode=1, lanes_per_system=lanes)
+    o = oracle_run(orc, ens, 500, gr_mode=1)
+    assert_parity(g, o, 1e-10, ens.n_planets)
 
 
 @pytest.mark.parametrize("nmax", [1, 2, 3, 4, 5])
@@ -152,9 +154,9 @@ def test_lanes_per_system_variants(whg, orc, nmax):
                           ens.vel[:, :1 + nmax].copy(), np.minimum(ens.n_planets, nmax), ens.dt)
     ens = inputs._assemble(1.0, ens.masses[:, 1:], ens.pos[:, 1:] - ens.pos[:, :1],
                            ens.vel[:, 1:] - ens.vel[:, :1], ens.n_planets, ens.dt, "")
-    g = gpu_run(whg, ens, 1000, gr_mode=1)
-    o = oracle_run(orc, ens, 1000, gr_mode=1)
-    assert_parity(g, o, 1e-9, ens.n_planets)
+    g = gpu_run(whg, ens, 500, gr_mode=1)
+    o = oracle_run(orc, ens, 500, gr_mode=1)
+    assert_parity(g, o, 1e-10, ens.n_planets)
 
 
 def test_massless_test_particles(whg, orc):
