@@ -89,6 +89,28 @@ def dist_env():
     return rank, world, local
 
 
+def rank_workload(args, rank: int):
+    """Weak scaling: every rank integrates its own ensemble of args.systems
+    systems (seed + rank); no system is shared between ranks."""
+    return inputs.solar_ensemble(args.seed + rank, args.systems)
+
+
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """Maximum of a per-rank float over all ranks (the slowest rank sets the
+    elapsed time of a weak-scaling step); identity without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, systems: int, chunk: int, steps: int, max_ms: float) -> float:
+    """Whole-job system-steps/s: all ranks' system-steps over the slowest rank's time."""
+    return world * systems * chunk * steps / (max_ms / 1e3)
+
+
 def kernel_source_hash() -> str:
     """Hash of the sources that define the step kernel (device code and its
     instantiation for 8 lanes per system)."""
@@ -204,7 +226,7 @@ def run_whg(args):
         dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
     build.build()
     S, chunk = args.systems, args.chunk
-    ens = inputs.solar_ensemble(args.seed + rank, S)
+    ens = rank_workload(args, rank)
     stream = torch.cuda.Stream()
     it = whg.Integrator(S, 8, gr_mode=args.gr_mode, block_size=args.block_size,
                         stream=stream.cuda_stream)
@@ -240,12 +262,8 @@ def run_whg(args):
             dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = float(sum(step_ms))
-    worst = total_ms
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        worst = float(t.item())
-    value = world * S * chunk * args.steps / (worst / 1e3)
+    worst = max_over_ranks(total_ms, dist, "cuda")
+    value = job_throughput(world, S, chunk, args.steps, worst)
     launches_per_step = launches / args.steps
 
     # end to end through the public API: pinned host inputs -> init (H2D) ->
@@ -273,12 +291,8 @@ def run_whg(args):
         it.step(chunk)
         whg.whg_read_state(it.ctx, out["pos"].numpy(), out["vel"].numpy(), out["status"].numpy(),
                            out["t"].numpy())
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * S * chunk * args.e2e_steps / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e_value = job_throughput(world, S, chunk, args.e2e_steps, 1e3 * e2e_s)
     bad = int((out["status"].numpy() != 0).sum())
 
     if rank != 0:
