@@ -66,7 +66,8 @@ def _load():
         L = ctypes.POINTER(ctypes.c_longlong)
         lib.orc_create.restype = P
         lib.orc_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_double, ctypes.c_double]
         lib.orc_destroy.argtypes = [P]
         lib.orc_init.argtypes = [P, D, D, D, I, D]
         lib.orc_init.restype = ctypes.c_int
@@ -105,12 +106,14 @@ class OracleEnsemble:
 
     def __init__(self, n_systems: int, max_planets: int, gr_mode: int = 0,
                  c_light: float = C_LIGHT_DEFAULT, newton_terms: int = 8,
-                 halley_terms: int = 4, halley_iters: int = 2, newton_iters: int = 2):
+                 halley_terms: int = 4, halley_iters: int = 2, newton_iters: int = 2,
+                 encounter_hill: float = 0.0, eject_factor: float = 0.0):
         self._lib = _load()
         self.S, self.N = int(n_systems), int(max_planets)
         self._h = self._lib.orc_create(self.S, self.N, int(gr_mode), float(c_light),
                                        int(halley_iters), int(halley_terms),
-                                       int(newton_iters), int(newton_terms))
+                                       int(newton_iters), int(newton_terms),
+                                       float(encounter_hill), float(eject_factor))
         if not self._h:
             raise ValueError("orc_create: invalid arguments")
 

@@ -36,6 +36,7 @@ static Counted operator-(Counted a, double b) { return a - Counted(b); }
 static Counted operator*(Counted a, double b) { return a * Counted(b); }
 static Counted operator/(Counted a, double b) { return a / Counted(b); }
 static bool operator>(Counted a, double b) { return a.v > b; }
+static bool operator<(Counted a, double b) { return a.v < b; }
 static Counted orc_sqrt(Counted x) { ++Counted::sqrts; return Counted(std::sqrt(x.v)); }
 static int orc_isfinite(Counted x) { return std::isfinite(x.v) ? 1 : 0; }
 
@@ -50,6 +51,7 @@ int main(int argc, char** argv)
     orc_options opt;
     opt.gr_mode = gr; opt.c_light = 10065.32; opt.halley_iters = 2; opt.halley_terms = 4;
     opt.newton_iters = 2; opt.newton_terms = nt;
+    opt.encounter_hill = 0.0; opt.eject_factor = 0.0;
     orc_system s = orc_system();
     s.n = n; s.m0 = 1.0; s.dt = 0.01; s.M = 1.0; s.nstep = 1;   /* steady state: K(dt) */
     for (int i = 0; i < n; ++i) {

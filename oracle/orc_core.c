@@ -35,6 +35,12 @@
  *   - a system whose step produces a non-finite value, or that starts a
  *     Kepler drift with beta <= 0 (unbound; outside the solver's domain,
  *     Sec. 3.2), is rolled back to the start of that step and frozen.
+ *   - optional ensemble stopping rules (not part of the paper's map), with the
+ *     same rollback: a pair closer than K mutual Hill radii
+ *     ((m_i+m_j)/(3 m_0))^(1/3) (a_i+a_j)/2 during the interaction step, or a
+ *     planet farther than F times the system's largest initial a at the start
+ *     of a drift; a_i are the osculating heliocentric semi-major axes
+ *     (mu = G(m_0+m_i)) of the initial state.
  *
  * This file is C99 and also compiles as C++ with ORC_REAL set to a counting
  * number type (oracle/flopcount.cpp); that build only counts operations.
@@ -57,6 +63,8 @@ typedef ORC_REAL orc_real;
 
 #define ORC_STATUS_NONFINITE 1
 #define ORC_STATUS_HYPERBOLIC 2
+#define ORC_STATUS_CLOSE_ENCOUNTER 8
+#define ORC_STATUS_EJECTED 16
 
 typedef struct {
     int gr_mode;         /* 0 off, 1 canonical, 2 with explicit back-reaction */
@@ -65,6 +73,8 @@ typedef struct {
     int halley_terms;    /* 4 (Sec. 3.2) */
     int newton_iters;    /* 2 (Sec. 3.2) */
     int newton_terms;    /* 8 (Sec. 3.2) or 6 (Appendix A) */
+    double encounter_hill; /* stop rule: pair closer than this many mutual Hill radii (0 = off) */
+    double eject_factor;   /* stop rule: |Q_i| beyond this many initial outermost a (0 = off) */
 } orc_options;
 
 /* One system in democratic heliocentric coordinates (Sec. 3.1).
@@ -81,6 +91,7 @@ typedef struct {
     double Xcm[3], Vcm[3];      /* barycentre position (at t = 0) and velocity */
     long long nstep;            /* completed steps; 0 = synchronized state */
     int status;
+    double a0[ORC_NMAX];        /* osculating heliocentric semi-major axes at init (stop rules) */
 } orc_system;
 
 /* 1/k! for the Stumpff series: k! is exact in double for k <= 22, so one
@@ -193,11 +204,13 @@ static void orc_jump(orc_system* s, double h)
 /* Interaction kick H_I for time h (Sec. 3.3, Eq. 5):
  * a_i = -sum_{j != i} G m_j Q_ij / |Q_ij|^3 with Q_ij = Q_i - Q_j; v_i += h a_i.
  * Each unordered pair i < j is visited once and gives both accelerations
- * (Newton's third law, as Sec. 3.3 does to halve the square roots). */
-static void orc_interaction(orc_system* s, double h)
+ * (Newton's third law, as Sec. 3.3 does to halve the square roots).
+ * Returns 1 if a pair is closer than the close-encounter stop rule allows
+ * (not part of the paper's map: an ensemble stopping rule, see orc_step). */
+static int orc_interaction(orc_system* s, double h, const orc_options* opt)
 {
     orc_real a[ORC_NMAX][3];
-    int i, j, c;
+    int i, j, c, close = 0;
     for (i = 0; i < s->n; ++i)
         for (c = 0; c < 3; ++c) a[i][c] = 0.0;
     for (i = 0; i < s->n; ++i) {
@@ -205,6 +218,12 @@ static void orc_interaction(orc_system* s, double h)
             orc_real d[3], r2, r3, ki, kj;
             for (c = 0; c < 3; ++c) d[c] = s->Q[i][c] - s->Q[j][c];
             r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (opt->encounter_hill > 0.0) {
+                /* mutual Hill radius from the initial semi-major axes */
+                double rh = opt->encounter_hill * cbrt((s->m[i] + s->m[j]) / (3.0 * s->m0)) *
+                            0.5 * (s->a0[i] + s->a0[j]);
+                if (r2 < rh * rh) close = 1;
+            }
             r3 = r2 * orc_sqrt(r2);
             ki = s->m[j] / r3;
             kj = s->m[i] / r3;
@@ -216,6 +235,7 @@ static void orc_interaction(orc_system* s, double h)
     }
     for (i = 0; i < s->n; ++i)
         for (c = 0; c < 3; ++c) s->v[i][c] = s->v[i][c] + h * a[i][c];
+    return close;
 }
 
 /* Acceleration from the 1/r^2 potential centred on the star (Sec. 3.3, GR
@@ -273,14 +293,23 @@ static void orc_step(orc_system* s, long long n, const orc_options* opt)
         memcpy(vs, s->v, sizeof(vs));
         {
             double hK = (s->nstep == 0) ? 0.5 * s->dt : s->dt;
+            double rej = 0.0;
+            if (opt->eject_factor > 0.0) {
+                for (i = 0; i < s->n; ++i)
+                    if (s->a0[i] > rej) rej = s->a0[i];
+                rej *= opt->eject_factor;
+            }
             for (i = 0; i < s->n; ++i) {
                 orc_real beta;
+                if (opt->eject_factor > 0.0 &&
+                    s->Q[i][0] * s->Q[i][0] + s->Q[i][1] * s->Q[i][1] + s->Q[i][2] * s->Q[i][2] > rej * rej)
+                    bad |= ORC_STATUS_EJECTED;
                 orc_kepler_drift(s->m0, hK, s->Q[i], s->v[i], opt, &beta);
                 if (!(beta > 0.0)) bad |= ORC_STATUS_HYPERBOLIC;
             }
         }
         orc_jump(s, 0.5 * s->dt);
-        orc_interaction(s, s->dt);
+        if (orc_interaction(s, s->dt, opt)) bad |= ORC_STATUS_CLOSE_ENCOUNTER;
         if (opt->gr_mode) orc_gr_kick(s, s->dt, opt);
         orc_jump(s, 0.5 * s->dt);
         if (!orc_state_finite(s)) bad |= ORC_STATUS_NONFINITE;

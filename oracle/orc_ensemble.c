@@ -25,7 +25,8 @@ typedef struct {
 } orc_ensemble;
 
 orc_ensemble* orc_create(int S, int Nmax, int gr_mode, double c_light, int halley_iters,
-                         int halley_terms, int newton_iters, int newton_terms)
+                         int halley_terms, int newton_iters, int newton_terms,
+                         double encounter_hill, double eject_factor)
 {
     orc_ensemble* e;
     if (S < 1 || Nmax < 1 || Nmax > ORC_NMAX) return NULL;
@@ -43,6 +44,8 @@ orc_ensemble* orc_create(int S, int Nmax, int gr_mode, double c_light, int halle
     e->opt.halley_terms = halley_terms;
     e->opt.newton_iters = newton_iters;
     e->opt.newton_terms = newton_terms;
+    e->opt.encounter_hill = encounter_hill;
+    e->opt.eject_factor = eject_factor;
     return e;
 }
 
@@ -75,11 +78,17 @@ static void orc_to_dh(orc_system* s, int n, const double* m, const double* x, co
         s->Vcm[c] = pu / s->M;
     }
     for (i = 0; i < n; ++i) {
+        double r2 = 0.0, w2 = 0.0;
         s->m[i] = m[1 + i];
         for (c = 0; c < 3; ++c) {
-            s->Q[i][c] = x[3 * (1 + i) + c] - x[c];
+            double dx = x[3 * (1 + i) + c] - x[c], du = u[3 * (1 + i) + c] - u[c];
+            s->Q[i][c] = dx;
             s->v[i][c] = u[3 * (1 + i) + c] - s->Vcm[c];
+            r2 += dx * dx;
+            w2 += du * du;
         }
+        /* heliocentric two-body osculating semi-major axis, mu = G (m_0 + m_i) */
+        s->a0[i] = 1.0 / (2.0 / sqrt(r2) - w2 / (m[0] + m[1 + i]));
     }
     s->nstep = 0;
     s->status = 0;
@@ -227,7 +236,7 @@ void orc_apply_substep(orc_ensemble* e, int s, int which, double h)
         for (i = 0; i < sy->n; ++i) orc_kepler_drift(sy->m0, h, sy->Q[i], sy->v[i], &e->opt, &beta);
         break;
     case 1: orc_jump(sy, h); break;
-    case 2: orc_interaction(sy, h); break;
+    case 2: orc_interaction(sy, h, &e->opt); break;
     case 3: orc_gr_kick(sy, h, &e->opt); break;
     default: break;
     }
