@@ -113,10 +113,10 @@ def job_throughput(world: int, systems: int, chunk: int, steps: int, max_ms: flo
 
 def kernel_source_hash() -> str:
     """Hash of the sources that define the step kernel (device code and its
-    instantiation for 8 lanes per system)."""
+    instantiation with 8-term Newton-phase series)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2307_05683_gb300", "csrc")
-    for name in ("whg_device.cuh", "whg_kernels_g8.cu"):
+    for name in ("whg_device.cuh", "whg_kernels_nt8.cu"):
         h.update(name.encode())
         h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:16]

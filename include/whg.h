@@ -28,7 +28,8 @@
  * code and records a message retrievable with whg_last_error().  Numerical
  * trouble inside one system is not an error: it sets that system's status
  * bits (WHG_STATUS_*), rolls the system back to the start of the failing step
- * and freezes it; all other systems continue.
+ * and freezes it; all other systems continue.  The optional stop rules
+ * (close encounter, ejection) end a system the same way.
  *
  * Threads and streams: a context is not thread-safe.  All device work of a
  * context is issued on the stream given to whg_create / whg_set_stream (NULL =
@@ -54,6 +55,10 @@ extern "C" {
 #define WHG_STATUS_HYPERBOLIC 2  /* a Kepler drift started with beta = 2 m0/r - v^2 <= 0
                                     (unbound orbit: outside the fixed solver's domain, Sec. 3.2) */
 #define WHG_STATUS_INVALID 4     /* rejected input (device-pointer init only) */
+#define WHG_STATUS_CLOSE_ENCOUNTER 8  /* stop rule: a pair closer than close_encounter_hill
+                                         mutual Hill radii during an interaction step */
+#define WHG_STATUS_EJECTED 16    /* stop rule: a planet beyond eject_factor x the system's
+                                    largest initial semi-major axis at the start of a step */
 
 #define WHG_MAX_PLANETS 8
 
@@ -71,10 +76,19 @@ typedef struct {
     int newton_terms;         /* Stumpff series terms in the Newton phase: 8 (default,
                                  Sec. 3.2) or 6 (Appendix A).  The Halley phase always
                                  uses 4 terms; 2 Halley + 2 Newton iterations (Sec. 3.2). */
-    int lanes_per_system;     /* 0 = auto (smallest power of two >= max_planets), else
-                                 1, 2, 4 or 8 (>= max_planets): GPU lanes per system */
+    int lanes_per_system;     /* 0 = auto: systems are grouped by planet count n and a
+                                 system gets n warp lanes (8 for n = 7), floor(32/n)
+                                 systems per warp, all groups in one launch.  1..8
+                                 (>= max_planets): that many lanes for every system */
     int block_size;           /* CUDA threads per block, 0 = auto (multiple of 32) */
     long long steps_per_launch; /* 0 = auto; bounds one kernel launch's length */
+    double close_encounter_hill; /* ensemble stop rule (not in the paper's map), 0 = off:
+                                 stop a system when a pair comes closer than this many
+                                 mutual Hill radii ((m_i+m_j)/(3 m0))^(1/3) (a_i+a_j)/2,
+                                 a_i = initial osculating heliocentric semi-major axes */
+    double eject_factor;      /* ensemble stop rule, 0 = off: stop a system when a planet
+                                 is farther from the star than this factor times the
+                                 system's largest initial a at the start of a step */
 } whg_options;
 
 /* Fill *opt with the defaults above. */
@@ -103,8 +117,11 @@ int whg_init(whg_ctx* ctx, const double* masses, const double* pos, const double
              const int* n_planets, const double* dt);
 
 /* As whg_init, but all pointers are DEVICE pointers (same layouts) on ctx's
- * device, read on ctx's stream (async).  Invalid systems are not reported by
- * the return value: they get WHG_STATUS_INVALID and stay frozen. */
+ * device, read on ctx's stream.  With lanes_per_system = 0 and n_planets
+ * given, the planet counts are copied back to the host once to lay the
+ * ensemble out.  Returns after the init kernel has run.  Invalid systems are
+ * not reported by the return value: they get WHG_STATUS_INVALID and stay
+ * frozen. */
 int whg_init_device(whg_ctx* ctx, const double* masses, const double* pos, const double* vel,
                     const int* n_planets, const double* dt);
 
@@ -162,15 +179,18 @@ void whg_destroy(whg_ctx* ctx);
  * Does what whg_create + whg_init_device + whg_step(n_steps) +
  * whg_read_state_device would do, with the same kernels and results, but
  * calls no cudaMalloc, cudaFree or other allocating routine: the working state
- * lives in one fixed array of about 9 MiB in the library's device memory,
+ * lives in one fixed array of 10 MiB in the library's device memory,
  * which every GPU that loads the library holds until the process exits.
  * All array pointers are DEVICE pointers with the layouts above (n_planets,
  * status_out and t_out may be NULL); work is issued on cuda_stream (NULL =
  * legacy default stream) and the call returns after enqueueing it.
  *
- * Limit: n_systems x lanes per system (padded up to whole CUDA blocks) must
- * not exceed WHG_NOALLOC_MAX_LANES, e.g. 8192 systems of 5..8 planets with the
- * default 32-thread blocks; larger requests fail with WHG_EINVAL.
+ * Every system gets the same lane group (opt->lanes_per_system, or by default
+ * the group a context would use for max_planets planets), so results match a
+ * context created with that lanes_per_system.
+ * Limit: the warps needed (floor(32 / lanes) systems each) must not exceed
+ * WHG_NOALLOC_MAX_LANES / 32 lanes' worth, e.g. 8192 systems of 7 or 8
+ * planets; larger requests fail with WHG_EINVAL.
  * The first call on each device looks up the array's device address; make
  * that first call before any stream capture.
  * Every call reuses the same array and leaves its contents behind; each call

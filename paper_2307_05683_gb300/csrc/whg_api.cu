@@ -1,7 +1,8 @@
 // whg_api.cu -- host side of libwhg: the C ABI declared in include/whg.h.
 //
-// A context owns the ensemble's device state (structure of arrays, lane index
-// s * G + p) and staging buffers for host I/O.  Every operation is a kernel on
+// A context owns the ensemble's device state (structure of arrays; systems
+// grouped by planet count, see whg_internal.h) and staging buffers for host
+// I/O.  Every operation is a kernel on
 // the context's stream; host-pointer calls add one cudaMemcpyAsync each way and
 // wait for it.  Inputs given as host arrays are validated on the host.
 #include <cmath>
@@ -10,18 +11,20 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "whg_internal.h"
 
 struct whg_ctx {
-    int S, Nmax, G, S_pad, block;
+    int S, Nmax, block, Lfixed, warps_cap;
     whg_options opt;
     cudaStream_t stream;
     int device;
     bool initialized;
     long long launches;
     WhgState st;
-    const WhgKernels* kern;
+    WhgBuckets bk;
+    int* perm_d;              // [S] device copy of the internal -> caller permutation
     // staging for host I/O (device memory)
     double* stage_d;          // S * (7 * (1 + Nmax) + 1) doubles
     int* stage_i;             // 2 * S ints
@@ -54,24 +57,75 @@ int cuda_fail(whg_ctx* c, cudaError_t e, const char* what)
         if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);   \
     } while (0)
 
-const WhgKernels* kernels_for(int G)
-{
-    switch (G) {
-    case 1: return &whg_kernels_g1;
-    case 2: return &whg_kernels_g2;
-    case 4: return &whg_kernels_g4;
-    case 8: return &whg_kernels_g8;
-    default: return nullptr;
-    }
-}
-
 WhgLaunch launch_cfg(const whg_ctx* c)
 {
     WhgLaunch l;
     l.block = c->block;
-    l.grid = (int)(((long long)c->S_pad * c->G) / c->block);
+    const long long threads = (long long)c->bk.warp0[c->bk.nb] * 32;
+    l.grid = (int)((threads + c->block - 1) / c->block);
+    if (l.grid < 1) l.grid = 1;
     l.stream = c->stream;
     return l;
+}
+
+int systems_per_warp(int L) { return 32 / L; }
+
+// Warps needed in the worst case of planet-count mix (packed) or for the
+// fixed lane count.
+int warps_capacity(int S, int Nmax, int Lfixed)
+{
+    if (Lfixed) return (S + systems_per_warp(Lfixed) - 1) / systems_per_warp(Lfixed);
+    int spw_min = 32;
+    for (int n = 1; n <= Nmax; ++n) {
+        const int spw = systems_per_warp(whg_lanes_for_planets(n));
+        if (spw < spw_min) spw_min = spw;
+    }
+    return (S + spw_min - 1) / spw_min + 8;
+}
+
+// Bucket systems by lanes per system.  nplan may be null (all Nmax planets).
+// perm receives, for every internal system, the caller's index; returns
+// false (and fills nothing) when the layout is the identity.
+bool plan_layout(int S, int Nmax, int Lfixed, const int* nplan, WhgBuckets* bk, int* perm)
+{
+    *bk = WhgBuckets{};
+    if (Lfixed || !nplan) {
+        const int L = Lfixed ? Lfixed : whg_lanes_for_planets(Nmax);
+        bk->nb = 1;
+        bk->L[0] = L;
+        bk->warp0[0] = 0;
+        bk->warp0[1] = (S + systems_per_warp(L) - 1) / systems_per_warp(L);
+        bk->sys0[0] = 0;
+        bk->sys0[1] = S;
+        return false;
+    }
+    int count[9] = {0};
+    auto lanes_of = [&](int s) {
+        const int n = nplan[s];
+        return whg_lanes_for_planets(n >= 1 && n <= Nmax ? n : Nmax);   // invalid: frozen anyway
+    };
+    for (int s = 0; s < S; ++s) count[lanes_of(s)] += 1;
+    int next[9] = {0}, nb = 0, warps = 0, sys = 0;
+    for (int L = 1; L <= 8; ++L) {
+        if (!count[L]) continue;
+        bk->L[nb] = L;
+        bk->warp0[nb] = warps;
+        bk->sys0[nb] = sys;
+        next[L] = sys;
+        warps += (count[L] + systems_per_warp(L) - 1) / systems_per_warp(L);
+        sys += count[L];
+        ++nb;
+    }
+    bk->nb = nb;
+    bk->warp0[nb] = warps;
+    bk->sys0[nb] = S;
+    bool identity = true;
+    for (int s = 0; s < S; ++s) {
+        const int i = next[lanes_of(s)]++;
+        perm[i] = s;
+        identity &= (i == s);
+    }
+    return !identity;
 }
 
 bool finite(double x) { return std::isfinite(x); }
@@ -128,6 +182,8 @@ void whg_default_options(whg_options* opt)
     opt->lanes_per_system = 0;
     opt->block_size = 0;
     opt->steps_per_launch = 0;
+    opt->close_encounter_hill = 0.0;
+    opt->eject_factor = 0.0;
 }
 
 int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options* opt_in,
@@ -146,14 +202,13 @@ int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options*
         return fail(nullptr, WHG_EINVAL, "c_light=%g must be > 0", opt.c_light);
     if (opt.newton_terms != 6 && opt.newton_terms != 8)
         return fail(nullptr, WHG_EINVAL, "newton_terms=%d must be 6 or 8", opt.newton_terms);
-    int G = opt.lanes_per_system;
-    if (G == 0) {
-        G = 1;
-        while (G < max_planets) G <<= 1;
-    }
-    if (!kernels_for(G) || G < max_planets)
-        return fail(nullptr, WHG_EINVAL, "lanes_per_system=%d must be 1, 2, 4 or 8 and >= max_planets",
+    const int Lfixed = opt.lanes_per_system;
+    if (Lfixed < 0 || Lfixed > 8 || (Lfixed && Lfixed < max_planets))
+        return fail(nullptr, WHG_EINVAL, "lanes_per_system=%d must be 0 or in max_planets..8",
                     opt.lanes_per_system);
+    if (opt.close_encounter_hill < 0.0 || !std::isfinite(opt.close_encounter_hill) ||
+        opt.eject_factor < 0.0 || !std::isfinite(opt.eject_factor))
+        return fail(nullptr, WHG_EINVAL, "stop rules must be finite and >= 0");
     int block = opt.block_size ? opt.block_size : 32;
     if (block < 32 || block > WHG_MAX_BLOCK || block % 32)
         return fail(nullptr, WHG_EINVAL, "block_size=%d must be a multiple of 32 in 32..%d", block,
@@ -165,23 +220,21 @@ int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options*
     if (!c) return fail(nullptr, WHG_ENOMEM, "host allocation failed");
     c->S = n_systems;
     c->Nmax = max_planets;
-    c->G = G;
+    c->Lfixed = Lfixed;
     c->block = block;
-    const int per_block = block / G;
-    c->S_pad = (int)(((long long)n_systems + per_block - 1) / per_block * per_block);
+    c->warps_cap = warps_capacity(n_systems, max_planets, Lfixed);
     c->opt = opt;
     c->stream = (cudaStream_t)cuda_stream;
-    c->kern = kernels_for(G);
     cudaError_t e = cudaGetDevice(&c->device);
     if (e != cudaSuccess) {
         delete c;
         return fail(nullptr, WHG_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     }
 
-    const size_t L = (size_t)c->S_pad * G, P = (size_t)c->S_pad;
-    const size_t nd = 7 * L + 9 * P;
+    const size_t L = (size_t)c->warps_cap * 32, P = (size_t)n_systems;
+    const size_t nd = 8 * L + 10 * P;
     void* base = nullptr;
-    size_t bytes = nd * sizeof(double) + 2 * P * sizeof(int) + P * sizeof(long long);
+    size_t bytes = nd * sizeof(double) + P * sizeof(long long) + 3 * P * sizeof(int);
     e = cudaMalloc(&base, bytes);
     if (e != cudaSuccess) {
         delete c;
@@ -196,20 +249,25 @@ int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options*
     st.vx = d; d += L;
     st.vy = d; d += L;
     st.vz = d; d += L;
+    st.a0 = d; d += L;
     st.m0 = d; d += P;
     st.dt = d; d += P;
     st.M = d; d += P;
     st.xcm = d; d += 3 * P;
     st.vcm = d; d += 3 * P;
+    st.rej2 = d; d += P;
     long long* ll = (long long*)d;
     st.nstep = ll; ll += P;
     int* ip = (int*)ll;
     st.nplan = ip; ip += P;
-    st.status = ip;
+    st.status = ip; ip += P;
+    c->perm_d = ip;
+    st.perm = nullptr;
     st.S = n_systems;
-    st.S_pad = c->S_pad;
     st.Nmax = max_planets;
     st.c_light = opt.c_light;
+    st.hill = opt.close_encounter_hill;
+    st.eject = opt.eject_factor;
 
     const size_t B = 1 + (size_t)max_planets;
     const size_t sd = (size_t)n_systems * (7 * B + 1);
@@ -236,12 +294,25 @@ int whg_set_stream(whg_ctx* c, void* cuda_stream)
     return WHG_OK;
 }
 
-static int init_common(whg_ctx* c, const WhgIn& in)
+// Lay the ensemble out by planet count (nplan_host: caller's n_planets on the
+// host, or null) and run the init kernel on the inputs `in`.
+static int init_common(whg_ctx* c, const WhgIn& in, const int* nplan_host)
 {
-    WhgLaunch l = launch_cfg(c);
-    int rc = launch_check(c, c->kern->init(c->st, in, l), "init kernel");
+    std::vector<int> perm((size_t)c->S);
+    const bool permuted = plan_layout(c->S, c->Nmax, c->Lfixed, nplan_host, &c->bk, perm.data());
+    if (c->bk.warp0[c->bk.nb] > c->warps_cap)
+        return fail(c, WHG_EINVAL, "internal layout exceeds capacity");
+    if (permuted) {
+        WHG_CUDA(c, cudaMemcpyAsync(c->perm_d, perm.data(), perm.size() * sizeof(int),
+                                    cudaMemcpyHostToDevice, c->stream));
+        c->st.perm = c->perm_d;
+    } else {
+        c->st.perm = nullptr;
+    }
+    int rc = launch_check(c, whg_launch_init(c->st, c->bk, in, launch_cfg(c)), "init kernel");
     if (rc) return rc;
     c->initialized = true;
+    WHG_CUDA(c, cudaStreamSynchronize(c->stream));      // host buffers may be reused on return
     return WHG_OK;
 }
 
@@ -268,10 +339,7 @@ int whg_init(whg_ctx* c, const double* masses, const double* pos, const double* 
         WHG_CUDA(c, cudaMemcpyAsync(dn, n_planets, S * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     }
     WhgIn in{dm, dx, du, dn, ddt};
-    int rc = init_common(c, in);
-    if (rc) return rc;
-    WHG_CUDA(c, cudaStreamSynchronize(c->stream));      // host buffers may be reused on return
-    return WHG_OK;
+    return init_common(c, in, n_planets);
 }
 
 int whg_init_device(whg_ctx* c, const double* masses, const double* pos, const double* vel,
@@ -280,7 +348,14 @@ int whg_init_device(whg_ctx* c, const double* masses, const double* pos, const d
     if (!c) return WHG_EINVAL;
     if (!masses || !pos || !vel || !dt) return fail(c, WHG_EINVAL, "null input array");
     WhgIn in{masses, pos, vel, n_planets, dt};
-    return init_common(c, in);
+    if (n_planets && !c->Lfixed) {                       // the layout needs the planet counts
+        std::vector<int> np((size_t)c->S);
+        WHG_CUDA(c, cudaMemcpyAsync(np.data(), n_planets, np.size() * sizeof(int),
+                                    cudaMemcpyDeviceToHost, c->stream));
+        WHG_CUDA(c, cudaStreamSynchronize(c->stream));
+        return init_common(c, in, np.data());
+    }
+    return init_common(c, in, nullptr);
 }
 
 int whg_step(whg_ctx* c, long long n)
@@ -291,13 +366,13 @@ int whg_step(whg_ctx* c, long long n)
     long long chunk = c->opt.steps_per_launch;
     if (chunk <= 0) {
         // about 5e7 system-steps per launch (a few tenths of a second)
-        chunk = 50000000LL / (long long)c->S_pad;
+        chunk = 50000000LL / ((long long)c->bk.warp0[c->bk.nb] * 4 + 1);
         if (chunk < 1) chunk = 1;
     }
     WhgLaunch l = launch_cfg(c);
     while (n > 0) {
         const long long k = n < chunk ? n : chunk;
-        int rc = launch_check(c, c->kern->step(c->st, k, c->opt.newton_terms, c->opt.gr_mode, l),
+        int rc = launch_check(c, whg_launch_step(c->st, c->bk, k, c->opt.newton_terms, c->opt.gr_mode, l),
                               "step kernel");
         if (rc) return rc;
         n -= k;
@@ -314,7 +389,8 @@ int whg_read_state_device(whg_ctx* c, double* pos, double* vel, int* status, dou
     o.vel = vel;
     o.status = status;
     o.t = t;
-    return launch_check(c, c->kern->read(c->st, o, c->opt.newton_terms, launch_cfg(c)), "read kernel");
+    return launch_check(c, whg_launch_read(c->st, c->bk, o, c->opt.newton_terms, launch_cfg(c)),
+                        "read kernel");
 }
 
 int whg_read_state(whg_ctx* c, double* pos, double* vel, int* status, double* t)
@@ -344,7 +420,8 @@ int whg_energy_device(whg_ctx* c, double* E)
     if (!E) return fail(c, WHG_EINVAL, "null output array");
     WhgOut o{};
     o.E = E;
-    return launch_check(c, c->kern->energy(c->st, o, c->opt.newton_terms, c->opt.gr_mode, launch_cfg(c)),
+    return launch_check(c, whg_launch_energy(c->st, c->bk, o, c->opt.newton_terms, c->opt.gr_mode,
+                                             launch_cfg(c)),
                         "energy kernel");
 }
 
@@ -371,7 +448,7 @@ int whg_get_raw(whg_ctx* c, double* Q, double* v, long long* nstep, int* status)
     o.rawv = c->stage_d + S * N * 3;
     o.rawn = c->stage_l;
     o.status = c->stage_i;
-    int rc = launch_check(c, c->kern->raw(c->st, o, 0, launch_cfg(c)), "raw kernel");
+    int rc = launch_check(c, whg_launch_raw(c->st, c->bk, o, 0, launch_cfg(c)), "raw kernel");
     if (rc) return rc;
     WHG_CUDA(c, cudaMemcpyAsync(Q, o.rawQ, S * N * 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     WHG_CUDA(c, cudaMemcpyAsync(v, o.rawv, S * N * 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -401,7 +478,7 @@ int whg_set_raw(whg_ctx* c, const double* Q, const double* v, const long long* n
     o.inv = dv;
     o.inn = c->stage_l;
     o.ins = c->stage_i;
-    int rc = launch_check(c, c->kern->raw(c->st, o, 1, launch_cfg(c)), "raw kernel");
+    int rc = launch_check(c, whg_launch_raw(c->st, c->bk, o, 1, launch_cfg(c)), "raw kernel");
     if (rc) return rc;
     WHG_CUDA(c, cudaStreamSynchronize(c->stream));
     return WHG_OK;

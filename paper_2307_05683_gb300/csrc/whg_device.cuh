@@ -1,6 +1,7 @@
 // whg_device.cuh -- device code of libwhg: FP64 special functions, the
-// Wisdom-Holman sub-steps and the kernels, templated on the number G of warp
-// lanes per system (one lane per planet, G in {1, 2, 4, 8}).
+// Wisdom-Holman sub-steps and the kernel bodies, templated on the number L of
+// warp lanes per system (one lane per planet, L in 1..8, floor(32/L) systems
+// per warp).
 //
 // GB300 design notes.  The whole step is FP64 arithmetic on a few registers
 // per lane; on this part the FP64 pipe retires about 2 lanes per clock per SM
@@ -12,8 +13,9 @@
 //     third-order FP64 refinement (3 and 5 FP64 instructions);
 //   * the all-pairs interaction uses Newton's third law (Sec. 3.3), with
 //     partner schedules that suit warp shuffles rather than AVX512 lanes;
-//   * cross-lane sums are xor butterflies over the system's lanes (Sec. 3.4),
-//     so every lane gets the bitwise-identical total.
+//   * cross-lane sums are xor butterflies over the system's lanes (Sec. 3.4)
+//     when L is a power of two, else a gather in fixed lane order; either way
+//     every lane gets the bitwise-identical total.
 // State stays in registers for the whole launch; HBM is touched only at load
 // and store (coalesced: consecutive lanes read consecutive doubles).
 #pragma once
@@ -231,69 +233,114 @@ __device__ __forceinline__ bool kepler_drift(double mu, double h, double& qx, do
     return beta > 0.0;
 }
 
-// Sum of x over the G lanes of this system (xor butterfly, Sec. 3.4); every
-// lane receives the same bits because each level adds a commuting pair.
-template <int G>
-__device__ __forceinline__ double group_sum(double x)
+// ------------------------------------------------------------------------
+// Lane groups: L lanes per system, floor(32/L) systems per warp; lanes beyond
+// the last whole group hold no system.
+template <int L>
+struct Group {
+    static constexpr int SPW = 32 / L;     // systems per warp
+    int lane, slot, p, base;
+    bool in_group;
+    __device__ __forceinline__ Group()
+    {
+        lane = (int)(threadIdx.x & 31u);
+        slot = lane / L;
+        in_group = slot < SPW;
+        p = in_group ? lane - slot * L : 0;
+        base = slot * L;
+    }
+    // lane holding planet (p + k) mod L of this system (own lane outside groups)
+    __device__ __forceinline__ int at(int k) const
+    {
+        int q = p + k;
+        q = q >= L ? q - L : (q < 0 ? q + L : q);
+        return in_group ? base + q : lane;
+    }
+    __device__ __forceinline__ unsigned mask() const
+    {
+        return in_group ? (((L == 32) ? WHG_FULL_MASK : ((1u << L) - 1u)) << base) : (1u << lane);
+    }
+};
+
+// Sum of x over the system's lanes, the same bits in every lane: xor
+// butterfly (Sec. 3.4) for power-of-two L, else a fixed-order gather.
+template <int L>
+__device__ __forceinline__ double group_sum(const Group<L>& g, double x)
 {
+    if ((L & (L - 1)) == 0) {
 #pragma unroll
-    for (int o = 1; o < G; o <<= 1) x += __shfl_xor_sync(WHG_FULL_MASK, x, o, G);
-    return x;
+        for (int o = 1; o < L; o <<= 1) x += __shfl_xor_sync(WHG_FULL_MASK, x, o);
+        return x;
+    } else {
+        double s = __shfl_sync(WHG_FULL_MASK, x, g.in_group ? g.base : g.lane);
+#pragma unroll
+        for (int j = 1; j < L; ++j) s += __shfl_sync(WHG_FULL_MASK, x, g.in_group ? g.base + j : g.lane);
+        return s;
+    }
 }
 
 // Jump step (Sec. 3.4, Eq. 6): Q_i += (h/m0) sum_j m_j v_j; jc = h / m0.
-template <int G>
-__device__ __forceinline__ void jump(double m, double jc, double vx, double vy, double vz,
-                                     double& qx, double& qy, double& qz)
+template <int L>
+__device__ __forceinline__ void jump(const Group<L>& g, double m, double jc, double vx, double vy,
+                                     double vz, double& qx, double& qy, double& qz)
 {
-    const double px = group_sum<G>(m * vx);
-    const double py = group_sum<G>(m * vy);
-    const double pz = group_sum<G>(m * vz);
+    const double px = group_sum<L>(g, m * vx);
+    const double py = group_sum<L>(g, m * vy);
+    const double pz = group_sum<L>(g, m * vz);
     qx = fma(jc, px, qx);
     qy = fma(jc, py, qy);
     qz = fma(jc, pz, qz);
 }
 
 // Interaction kick (Sec. 3.3, Eq. 5) plus the GR term, for time dt, added
-// straight into v.  hm = dt m_i.  Pairs at cyclic lane distance k < G/2 are
-// evaluated once, by the lower lane of the pair, and the reaction is passed to
-// the partner by a shuffle (Newton's third law); the G/2 pairs at distance G/2
-// are evaluated by both of their lanes.  For G = 8 that is 4 reciprocal square
-// roots per lane for the 28 pairs, as in the paper, but with rotations that
-// cost the same on any lane pair of a warp.
-template <int G, int GRM>
-__device__ __forceinline__ void kick(int p, double qx, double qy, double qz, double hm,
-                                     double mrat, double kgr, double& vx, double& vy, double& vz)
+// straight into v; hm = dt m_i.  Pairs at cyclic lane distance k, 1 <= k <
+// L/2, are evaluated once, by the lane at the lower end of the rotation, and
+// the reaction is passed to the partner by a shuffle (Newton's third law);
+// for even L the L/2 pairs at distance L/2 are evaluated by both of their
+// lanes.  For L = 8 that is 4 reciprocal square roots per lane for the 28
+// pairs, as in the paper, with rotations that cost the same on any lanes of a
+// warp.  thr2[k-1] is the squared close-encounter distance of this lane's
+// pair at distance k (0 when the rule is off); returns true if a pair it
+// evaluates is closer (compared on the bit patterns of positive doubles, so
+// no FP64 instruction is spent).
+template <int L, int GRM>
+__device__ __forceinline__ bool kick(const Group<L>& g, double qx, double qy, double qz, double hm,
+                                     double mrat, double kgr, const double* thr2, double& vx,
+                                     double& vy, double& vz)
 {
+    bool close = false;
 #pragma unroll
-    for (int k = 1; k < G / 2; ++k) {
-        const int to = (p + k) & (G - 1);
-        const int from = (p - k) & (G - 1);
-        const double dx = __shfl_sync(WHG_FULL_MASK, qx, to, G) - qx;   // Q_j - Q_i
-        const double dy = __shfl_sync(WHG_FULL_MASK, qy, to, G) - qy;
-        const double dz = __shfl_sync(WHG_FULL_MASK, qz, to, G) - qz;
-        const double hmj = __shfl_sync(WHG_FULL_MASK, hm, to, G);
-        const double r3 = rsqrt_cubed(fma(dx, dx, fma(dy, dy, dz * dz)));
+    for (int k = 1; 2 * k < L; ++k) {
+        const int to = g.at(k), from = g.at(-k);
+        const double dx = __shfl_sync(WHG_FULL_MASK, qx, to) - qx;   // Q_j - Q_i
+        const double dy = __shfl_sync(WHG_FULL_MASK, qy, to) - qy;
+        const double dz = __shfl_sync(WHG_FULL_MASK, qz, to) - qz;
+        const double hmj = __shfl_sync(WHG_FULL_MASK, hm, to);
+        const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        close |= __double_as_longlong(r2) < __double_as_longlong(thr2[k - 1]);
+        const double r3 = rsqrt_cubed(r2);
         const double sj = hmj * r3;
         vx = fma(sj, dx, vx);
         vy = fma(sj, dy, vy);
         vz = fma(sj, dz, vz);
         const double si = hm * r3;                    // reaction on j: -si (Q_j - Q_i)
-        const double ex = __shfl_sync(WHG_FULL_MASK, dx, from, G);
-        const double ey = __shfl_sync(WHG_FULL_MASK, dy, from, G);
-        const double ez = __shfl_sync(WHG_FULL_MASK, dz, from, G);
-        const double es = __shfl_sync(WHG_FULL_MASK, si, from, G);
+        const double ex = __shfl_sync(WHG_FULL_MASK, dx, from);
+        const double ey = __shfl_sync(WHG_FULL_MASK, dy, from);
+        const double ez = __shfl_sync(WHG_FULL_MASK, dz, from);
+        const double es = __shfl_sync(WHG_FULL_MASK, si, from);
         vx = fma(-es, ex, vx);
         vy = fma(-es, ey, vy);
         vz = fma(-es, ez, vz);
     }
-    if (G >= 2) {
-        const int to = p ^ (G / 2);
-        const double dx = __shfl_sync(WHG_FULL_MASK, qx, to, G) - qx;
-        const double dy = __shfl_sync(WHG_FULL_MASK, qy, to, G) - qy;
-        const double dz = __shfl_sync(WHG_FULL_MASK, qz, to, G) - qz;
-        const double hmj = __shfl_sync(WHG_FULL_MASK, hm, to, G);
-        const double sj = hmj * rsqrt_cubed(fma(dx, dx, fma(dy, dy, dz * dz)));
+    if (L >= 2 && (L & 1) == 0) {
+        const int to = g.at(L / 2);
+        const double dx = __shfl_sync(WHG_FULL_MASK, qx, to) - qx;
+        const double dy = __shfl_sync(WHG_FULL_MASK, qy, to) - qy;
+        const double dz = __shfl_sync(WHG_FULL_MASK, qz, to) - qz;
+        const double hmj = __shfl_sync(WHG_FULL_MASK, hm, to);
+        const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        close |= __double_as_longlong(r2) < __double_as_longlong(thr2[L / 2 - 1]);
+        const double sj = hmj * rsqrt_cubed(r2);
         vx = fma(sj, dx, vx);
         vy = fma(sj, dy, vy);
         vz = fma(sj, dz, vz);
@@ -308,50 +355,68 @@ __device__ __forceinline__ void kick(int p, double qx, double qy, double qz, dou
             vz = fma(c, qz, vz);
         } else {
             const double ax = c * qx, ay = c * qy, az = c * qz;
-            const double bx = group_sum<G>(mrat * ax);
-            const double by = group_sum<G>(mrat * ay);
-            const double bz = group_sum<G>(mrat * az);
+            const double bx = group_sum<L>(g, mrat * ax);
+            const double by = group_sum<L>(g, mrat * ay);
+            const double bz = group_sum<L>(g, mrat * az);
             vx = vx + (ax - bx);
             vy = vy + (ay - by);
             vz = vz + (az - bz);
         }
     }
+    return close;
 }
 
-// Lane mask of the G lanes of this thread's system inside its warp.
-template <int G>
-__device__ __forceinline__ unsigned group_mask()
-{
-    const unsigned base = (threadIdx.x & 31u) & ~(unsigned)(G - 1);
-    return (G == 32 ? WHG_FULL_MASK : ((1u << G) - 1u)) << base;
-}
-
-// Far-away parking spot of padding lanes: distinct, finite, never updated.
+// Far-away parking spot of lanes without a planet: distinct, finite, fixed.
 __device__ __forceinline__ double parked_x(int p) { return 1.0e6 * (double)(p + 1); }
 
-// ------------------------------------------------------------------------
-// Kernels.  The grid covers exactly S_pad * G threads; thread t is lane
-// t % G of system t / G.  Shuffles use the full warp mask, so no thread
-// returns before the last shuffle.
+// Where a warp's lanes live: bucket b, warp wb inside it, this lane's system.
+template <int L>
+struct Place {
+    Group<L> g;
+    int sys;             // internal system index (valid only if has_sys)
+    bool has_sys;
+    size_t lane;         // index into the lane arrays
+    __device__ __forceinline__ Place(const WhgBuckets& bk, int b, int w)
+    {
+        const int sl = (w - bk.warp0[b]) * Group<L>::SPW + g.slot;
+        has_sys = g.in_group && sl < bk.sys0[b + 1] - bk.sys0[b];
+        sys = has_sys ? bk.sys0[b] + sl : 0;
+        lane = (size_t)w * 32 + g.lane;
+    }
+};
 
-template <int G>
-__global__ void __launch_bounds__(WHG_MAX_BLOCK) k_init(WhgState st, WhgIn in)
+__device__ __forceinline__ int user_index(const WhgState& st, int sys)
 {
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = tid / G, p = tid & (G - 1);
-    if (s >= st.S_pad) return;
-    const size_t lane = (size_t)s * G + p;
-    const int B = 1 + st.Nmax;
+    return st.perm ? st.perm[sys] : sys;
+}
+
+// ------------------------------------------------------------------------
+// Kernel bodies.  A warp belongs to one bucket; shuffles use the full warp
+// mask, so no lane leaves a body before its last shuffle.
+
+// Inertial -> DH (Sec. 3.1): Q_i = x_i - x_0, v_i = u_i - V_cm; M, X_cm, V_cm
+// kept; initial osculating a_i (mu = G(m0 + m_i)) for the stop rules.
+template <int L>
+__device__ __forceinline__ void init_body(const WhgState& st, const WhgBuckets& bk, const WhgIn& in,
+                                          int b, int w)
+{
+    const Place<L> pl(bk, b, w);
+    const int p = pl.g.p;
+    const size_t lane = pl.lane;
     int n = 0, ok = 0;
-    double mm = 0.0, M = 0.0, xc[3] = {0.0, 0.0, 0.0}, vc[3] = {0.0, 0.0, 0.0}, m0 = 1.0, dt = 1.0;
-    if (s < st.S) {
-        const double* ms = in.masses + (size_t)s * B;
-        const double* xs = in.pos + (size_t)s * B * 3;
-        const double* us = in.vel + (size_t)s * B * 3;
-        n = in.nplan ? in.nplan[s] : st.Nmax;
-        dt = in.dt[s];
+    double M = 0.0, xc[3] = {0.0, 0.0, 0.0}, vc[3] = {0.0, 0.0, 0.0}, m0 = 1.0, dt = 1.0e-3;
+    double amax = 0.0, a_mine = 0.0;
+    if (pl.has_sys) {
+        const int u = user_index(st, pl.sys);
+        const int B = 1 + st.Nmax;
+        const double* ms = in.masses + (size_t)u * B;
+        const double* xs = in.pos + (size_t)u * B * 3;
+        const double* us = in.vel + (size_t)u * B * 3;
+        n = in.nplan ? in.nplan[u] : st.Nmax;
+        dt = in.dt[u];
         m0 = ms[0];
-        ok = n >= 1 && n <= st.Nmax && dt > 0.0 && is_finite(dt) && m0 > 0.0 && is_finite(m0);
+        ok = n >= 1 && n <= st.Nmax && n <= L && dt > 0.0 && is_finite(dt) && m0 > 0.0 &&
+             is_finite(m0);
         if (ok) {
             for (int k = 0; k <= n; ++k) {
                 M += ms[k];
@@ -361,8 +426,19 @@ __global__ void __launch_bounds__(WHG_MAX_BLOCK) k_init(WhgState st, WhgIn in)
                     xc[c] += ms[k] * xs[3 * k + c];
                     vc[c] += ms[k] * us[3 * k + c];
                 }
-                if (k > 0)
+                if (k > 0) {
                     ok &= !(xs[3 * k] == xs[0] && xs[3 * k + 1] == xs[1] && xs[3 * k + 2] == xs[2]);
+                    double r2 = 0.0, w2 = 0.0;
+                    for (int c = 0; c < 3; ++c) {
+                        const double dx = __dsub_rn(xs[3 * k + c], xs[c]);
+                        const double du = __dsub_rn(us[3 * k + c], us[c]);
+                        r2 = __dadd_rn(r2, __dmul_rn(dx, dx));
+                        w2 = __dadd_rn(w2, __dmul_rn(du, du));
+                    }
+                    const double a = 1.0 / __dsub_rn(2.0 / sqrt(r2), w2 / __dadd_rn(m0, ms[k]));
+                    amax = fmax(amax, a);
+                    if (k == p + 1) a_mine = a;
+                }
             }
             for (int c = 0; c < 3; ++c) {
                 xc[c] /= M;
@@ -370,17 +446,17 @@ __global__ void __launch_bounds__(WHG_MAX_BLOCK) k_init(WhgState st, WhgIn in)
             }
         }
         if (ok && p < n) {
-            mm = ms[1 + p];
-            st.m[lane] = mm;
+            st.m[lane] = ms[1 + p];
             st.qx[lane] = xs[3 * (1 + p) + 0] - xs[0];
             st.qy[lane] = xs[3 * (1 + p) + 1] - xs[1];
             st.qz[lane] = xs[3 * (1 + p) + 2] - xs[2];
             st.vx[lane] = us[3 * (1 + p) + 0] - vc[0];
             st.vy[lane] = us[3 * (1 + p) + 1] - vc[1];
             st.vz[lane] = us[3 * (1 + p) + 2] - vc[2];
+            st.a0[lane] = a_mine;
         }
     }
-    if (!(ok && p < n)) {                            // padding lane or rejected system
+    if (!(ok && p < n)) {                            // no planet on this lane
         st.m[lane] = 0.0;
         st.qx[lane] = parked_x(p);
         st.qy[lane] = 0.0;
@@ -388,8 +464,10 @@ __global__ void __launch_bounds__(WHG_MAX_BLOCK) k_init(WhgState st, WhgIn in)
         st.vx[lane] = 0.0;
         st.vy[lane] = 0.0;
         st.vz[lane] = 0.0;
+        st.a0[lane] = 0.0;
     }
-    if (p == 0) {
+    if (pl.has_sys && p == 0) {
+        const int s = pl.sys;
         if (!ok) {
             m0 = 1.0;
             dt = 1.0e-3;
@@ -399,56 +477,82 @@ __global__ void __launch_bounds__(WHG_MAX_BLOCK) k_init(WhgState st, WhgIn in)
         st.dt[s] = dt;
         st.M[s] = M;
         for (int c = 0; c < 3; ++c) {
-            st.xcm[(size_t)c * st.S_pad + s] = xc[c];
-            st.vcm[(size_t)c * st.S_pad + s] = vc[c];
+            st.xcm[(size_t)c * st.S + s] = xc[c];
+            st.vcm[(size_t)c * st.S + s] = vc[c];
         }
+        const double rej = st.eject * amax;
+        st.rej2[s] = (st.eject > 0.0 && ok && amax > 0.0) ? rej * rej : __longlong_as_double(0x7ff0000000000000LL);
         st.nplan[s] = ok ? n : 0;
-        st.status[s] = (s < st.S && !ok) ? WHG_STATUS_INVALID : 0;
+        st.status[s] = ok ? 0 : WHG_STATUS_INVALID;
         st.nstep[s] = 0;
     }
 }
 
 // n Wisdom-Holman steps, state in registers (Eq. 2 with fused drifts).
-template <int G, int NT, int GRM>
-__global__ void __launch_bounds__(WHG_MAX_BLOCK) k_step(WhgState st, long long nsteps)
+template <int L, int NT, int GRM>
+__device__ __forceinline__ void step_body(const WhgState& st, const WhgBuckets& bk, int b, int w,
+                                          long long nsteps)
 {
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = tid / G, p = tid & (G - 1);
-    const size_t lane = (size_t)s * G + p;
+    const Place<L> pl(bk, b, w);
+    const Group<L>& g = pl.g;
+    const size_t lane = pl.lane;
+    const int s = pl.sys;
     const double m = st.m[lane];
     double qx = st.qx[lane], qy = st.qy[lane], qz = st.qz[lane];
     double vx = st.vx[lane], vy = st.vy[lane], vz = st.vz[lane];
-    const double mu = st.m0[s], dt = st.dt[s];
-    const int npl = st.nplan[s];
-    int status = st.status[s];
-    const long long nstep0 = st.nstep[s];
-    const bool real = s < st.S && p < npl;
-    bool alive = s < st.S && status == 0;
+    const double mu = pl.has_sys ? st.m0[s] : 1.0;
+    const double dt = pl.has_sys ? st.dt[s] : 1.0e-3;
+    const int npl = pl.has_sys ? st.nplan[s] : 0;
+    int status = pl.has_sys ? st.status[s] : 0;
+    const long long nstep0 = pl.has_sys ? st.nstep[s] : 0;
+    const double rej2 = pl.has_sys ? st.rej2[s] : 0.0;
+    const bool real = pl.has_sys && g.p < npl;
+    bool alive = pl.has_sys && status == 0;
     const double hm = dt * m;
     const double jc = (0.5 * dt) / mu;
     const double mrat = m / mu;
     const double kgr = GRM ? (-6.0 * mu * mu * dt) / (st.c_light * st.c_light) : 0.0;
-    const unsigned gmask = group_mask<G>();
+    // close-encounter distances of this lane's pairs (once per launch)
+    double thr2[4] = {0.0, 0.0, 0.0, 0.0};
+    {
+        const double a = st.a0[lane];
+#pragma unroll
+        for (int k = 1; 2 * k <= L; ++k) {
+            const int to = g.at(k);
+            const double mj = __shfl_sync(WHG_FULL_MASK, m, to);
+            const double aj = __shfl_sync(WHG_FULL_MASK, a, to);
+            if (st.hill > 0.0 && k - 1 < 4) {
+                const double rh = st.hill * cbrt((m + mj) / (3.0 * mu)) * 0.5 * (a + aj);
+                thr2[k - 1] = rh * rh;
+            }
+        }
+    }
+    const unsigned gmask = g.mask();
     long long done = 0;
     for (long long k = 0; k < nsteps; ++k) {
         if (!__any_sync(WHG_FULL_MASK, alive)) break;        // whole warp frozen
         const double sqx = qx, sqy = qy, sqz = qz, svx = vx, svy = vy, svz = vz;
         const double hK = (nstep0 + done == 0) ? 0.5 * dt : dt;
+        const double r0sq = fma(qx, qx, fma(qy, qy, qz * qz));
+        const bool far = __double_as_longlong(r0sq) > __double_as_longlong(rej2);
         const bool bound = kepler_drift<NT>(mu, hK, qx, qy, qz, vx, vy, vz);
-        jump<G>(m, jc, vx, vy, vz, qx, qy, qz);
-        kick<G, GRM>(p, qx, qy, qz, hm, mrat, kgr, vx, vy, vz);
-        jump<G>(m, jc, vx, vy, vz, qx, qy, qz);
+        jump<L>(g, m, jc, vx, vy, vz, qx, qy, qz);
+        const bool close = kick<L, GRM>(g, qx, qy, qz, hm, mrat, kgr, thr2, vx, vy, vz);
+        jump<L>(g, m, jc, vx, vy, vz, qx, qy, qz);
         const bool fin = is_finite(qx) & is_finite(qy) & is_finite(qz) & is_finite(vx) &
                          is_finite(vy) & is_finite(vz);
         const unsigned bad_h = __ballot_sync(WHG_FULL_MASK, real && !bound) & gmask;
         const unsigned bad_n = __ballot_sync(WHG_FULL_MASK, real && !fin) & gmask;
-        const bool ok = (bad_h | bad_n) == 0u;
-        if (!(alive && real && ok)) {                 // roll back: padding, frozen, failed
+        const unsigned bad_c = __ballot_sync(WHG_FULL_MASK, real && close) & gmask;
+        const unsigned bad_e = __ballot_sync(WHG_FULL_MASK, real && far) & gmask;
+        const bool ok = (bad_h | bad_n | bad_c | bad_e) == 0u;
+        if (!(alive && real && ok)) {                 // roll back: no planet, frozen, failed
             qx = sqx; qy = sqy; qz = sqz;
             vx = svx; vy = svy; vz = svz;
         }
         if (alive && !ok) {
-            status |= (bad_n ? WHG_STATUS_NONFINITE : 0) | (bad_h ? WHG_STATUS_HYPERBOLIC : 0);
+            status |= (bad_n ? WHG_STATUS_NONFINITE : 0) | (bad_h ? WHG_STATUS_HYPERBOLIC : 0) |
+                      (bad_c ? WHG_STATUS_CLOSE_ENCOUNTER : 0) | (bad_e ? WHG_STATUS_EJECTED : 0);
             alive = false;
         }
         done += alive ? 1 : 0;
@@ -457,7 +561,7 @@ __global__ void __launch_bounds__(WHG_MAX_BLOCK) k_step(WhgState st, long long n
         st.qx[lane] = qx; st.qy[lane] = qy; st.qz[lane] = qz;
         st.vx[lane] = vx; st.vy[lane] = vy; st.vz[lane] = vz;
     }
-    if (p == 0 && s < st.S) {
+    if (pl.has_sys && g.p == 0) {
         st.status[s] = status;
         st.nstep[s] = nstep0 + done;
     }
@@ -465,112 +569,116 @@ __global__ void __launch_bounds__(WHG_MAX_BLOCK) k_step(WhgState st, long long n
 
 // Synchronized copy (pending K(dt/2)) -> inertial frame (Sec. 3.1 inverted):
 // x_0 = X_cm + V_cm t - sum m_i Q_i / M, x_i = x_0 + Q_i,
-// u_0 = V_cm - sum m_i v_i / m0, u_i = v_i + V_cm.
-template <int G, int NT>
-__global__ void __launch_bounds__(WHG_MAX_BLOCK) k_read(WhgState st, WhgOut out)
+// u_0 = V_cm - sum m_i v_i / m0, u_i = v_i + V_cm.  Caller's order and layout.
+template <int L, int NT>
+__device__ __forceinline__ void read_body(const WhgState& st, const WhgBuckets& bk, const WhgOut& out,
+                                          int b, int w)
 {
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = tid / G, p = tid & (G - 1);
-    const size_t lane = (size_t)s * G + p;
+    const Place<L> pl(bk, b, w);
+    const Group<L>& g = pl.g;
+    const size_t lane = pl.lane;
+    const int s = pl.sys;
     const double m = st.m[lane];
     double qx = st.qx[lane], qy = st.qy[lane], qz = st.qz[lane];
     double vx = st.vx[lane], vy = st.vy[lane], vz = st.vz[lane];
-    const double mu = st.m0[s], dt = st.dt[s];
-    const long long ns = st.nstep[s];
+    const double mu = pl.has_sys ? st.m0[s] : 1.0;
+    const double dt = pl.has_sys ? st.dt[s] : 1.0e-3;
+    const long long ns = pl.has_sys ? st.nstep[s] : 0;
     if (ns > 0) kepler_drift<NT>(mu, 0.5 * dt, qx, qy, qz, vx, vy, vz);
-    const double sqx = group_sum<G>(m * qx), sqy = group_sum<G>(m * qy), sqz = group_sum<G>(m * qz);
-    const double spx = group_sum<G>(m * vx), spy = group_sum<G>(m * vy), spz = group_sum<G>(m * vz);
-    if (s >= st.S) return;                           // after the last shuffle
+    const double sqx = group_sum<L>(g, m * qx), sqy = group_sum<L>(g, m * qy), sqz = group_sum<L>(g, m * qz);
+    const double spx = group_sum<L>(g, m * vx), spy = group_sum<L>(g, m * vy), spz = group_sum<L>(g, m * vz);
+    if (!pl.has_sys) return;                         // after the last shuffle
     const int npl = st.nplan[s];
+    const int u = user_index(st, s);
     const int B = 1 + st.Nmax;
     const double t = (double)ns * dt;
     const double M = st.M[s];
-    double x0[3], u0[3];
-    const double sq[3] = {sqx, sqy, sqz}, sp[3] = {spx, spy, spz};
+    const double sq[3] = {sqx, sqy, sqz}, sp[3] = {spx, spy, spz}, q[3] = {qx, qy, qz}, v[3] = {vx, vy, vz};
+    double x0[3], u0[3], V[3];
     for (int c = 0; c < 3; ++c) {
-        const double X = st.xcm[(size_t)c * st.S_pad + s], V = st.vcm[(size_t)c * st.S_pad + s];
-        x0[c] = (X + V * t) - sq[c] / M;
-        u0[c] = V - sp[c] / mu;
+        const double X = st.xcm[(size_t)c * st.S + s];
+        V[c] = st.vcm[(size_t)c * st.S + s];
+        x0[c] = (X + V[c] * t) - sq[c] / M;
+        u0[c] = V[c] - sp[c] / mu;
     }
-    if (p < st.Nmax) {
-        const size_t o = ((size_t)s * B + 1 + p) * 3;
-        const bool live = p < npl;
-        if (out.pos) {
-            out.pos[o + 0] = live ? x0[0] + qx : 0.0;
-            out.pos[o + 1] = live ? x0[1] + qy : 0.0;
-            out.pos[o + 2] = live ? x0[2] + qz : 0.0;
-        }
-        if (out.vel) {
-            out.vel[o + 0] = live ? vx + st.vcm[s] : 0.0;
-            out.vel[o + 1] = live ? vy + st.vcm[(size_t)st.S_pad + s] : 0.0;
-            out.vel[o + 2] = live ? vz + st.vcm[(size_t)2 * st.S_pad + s] : 0.0;
+    for (int slot = g.p; slot < st.Nmax; slot += L) {    // planet slots of this lane
+        const size_t o = ((size_t)u * B + 1 + slot) * 3;
+        const bool live = slot == g.p && slot < npl;
+        for (int c = 0; c < 3; ++c) {
+            if (out.pos) out.pos[o + c] = live ? x0[c] + q[c] : 0.0;
+            if (out.vel) out.vel[o + c] = live ? v[c] + V[c] : 0.0;
         }
     }
-    if (p == 0) {
-        const size_t o = (size_t)s * B * 3;
+    if (g.p == 0) {
+        const size_t o = (size_t)u * B * 3;
         for (int c = 0; c < 3; ++c) {
             if (out.pos) out.pos[o + c] = x0[c];
             if (out.vel) out.vel[o + c] = u0[c];
         }
-        if (out.status) out.status[s] = st.status[s];
-        if (out.t) out.t[s] = t;
+        if (out.status) out.status[u] = st.status[s];
+        if (out.t) out.t[u] = t;
     }
 }
 
 // Energy of the synchronized state: H_0 + H_K + H_I + H_J (Eq. 1) [+ GR].
-template <int G, int NT, int GRM>
-__global__ void __launch_bounds__(WHG_MAX_BLOCK) k_energy(WhgState st, WhgOut out)
+template <int L, int NT, int GRM>
+__device__ __forceinline__ void energy_body(const WhgState& st, const WhgBuckets& bk,
+                                            const WhgOut& out, int b, int w)
 {
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = tid / G, p = tid & (G - 1);
-    const size_t lane = (size_t)s * G + p;
+    const Place<L> pl(bk, b, w);
+    const Group<L>& g = pl.g;
+    const size_t lane = pl.lane;
+    const int s = pl.sys;
     const double m = st.m[lane];
     double qx = st.qx[lane], qy = st.qy[lane], qz = st.qz[lane];
     double vx = st.vx[lane], vy = st.vy[lane], vz = st.vz[lane];
-    const double mu = st.m0[s], dt = st.dt[s];
-    if (st.nstep[s] > 0) kepler_drift<NT>(mu, 0.5 * dt, qx, qy, qz, vx, vy, vz);
+    const double mu = pl.has_sys ? st.m0[s] : 1.0;
+    const double dt = pl.has_sys ? st.dt[s] : 1.0e-3;
+    if (pl.has_sys && st.nstep[s] > 0) kepler_drift<NT>(mu, 0.5 * dt, qx, qy, qz, vx, vy, vz);
     const double r2 = fma(qx, qx, fma(qy, qy, qz * qz));
     double pair = 0.0;
 #pragma unroll
-    for (int k = 1; k < G; ++k) {
-        const int j = (p + k) & (G - 1);
-        const double dx = __shfl_sync(WHG_FULL_MASK, qx, j, G) - qx;
-        const double dy = __shfl_sync(WHG_FULL_MASK, qy, j, G) - qy;
-        const double dz = __shfl_sync(WHG_FULL_MASK, qz, j, G) - qz;
-        const double mj = __shfl_sync(WHG_FULL_MASK, m, j, G);
+    for (int k = 1; k < L; ++k) {
+        const int j = g.at(k);
+        const double dx = __shfl_sync(WHG_FULL_MASK, qx, j) - qx;
+        const double dy = __shfl_sync(WHG_FULL_MASK, qy, j) - qy;
+        const double dz = __shfl_sync(WHG_FULL_MASK, qz, j) - qz;
+        const double mj = __shfl_sync(WHG_FULL_MASK, m, j);
         pair += m * mj / sqrt(fma(dx, dx, fma(dy, dy, dz * dz)));
     }
     double part = 0.5 * m * fma(vx, vx, fma(vy, vy, vz * vz)) - mu * m / sqrt(r2) - 0.5 * pair;
     if (GRM != 0) part += -3.0 * m * mu * mu / (st.c_light * st.c_light * r2);
-    const double tot = group_sum<G>(part);
-    const double px = group_sum<G>(m * vx), py = group_sum<G>(m * vy), pz = group_sum<G>(m * vz);
-    if (s >= st.S || p != 0) return;
+    const double tot = group_sum<L>(g, part);
+    const double px = group_sum<L>(g, m * vx), py = group_sum<L>(g, m * vy), pz = group_sum<L>(g, m * vz);
+    if (!pl.has_sys || g.p != 0) return;
     double h0 = 0.0;
     for (int c = 0; c < 3; ++c) {
-        const double V = st.vcm[(size_t)c * st.S_pad + s];
+        const double V = st.vcm[(size_t)c * st.S + s];
         h0 += 0.5 * st.M[s] * V * V;
     }
-    out.E[s] = h0 + tot + (px * px + py * py + pz * pz) / (2.0 * mu);
+    out.E[user_index(st, s)] = h0 + tot + (px * px + py * py + pz * pz) / (2.0 * mu);
 }
 
-// Raw state copy between the lane arrays and the [S][Nmax][3] layout.
-template <int G>
-__global__ void __launch_bounds__(WHG_MAX_BLOCK) k_raw(WhgState st, WhgOut io, int set)
+// Raw state copy between the lane arrays and the caller's [S][Nmax][3] layout.
+template <int L>
+__device__ __forceinline__ void raw_body(const WhgState& st, const WhgBuckets& bk, const WhgOut& io,
+                                         int set, int b, int w)
 {
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = tid / G, p = tid & (G - 1);
-    if (s >= st.S) return;
-    const size_t lane = (size_t)s * G + p;
+    const Place<L> pl(bk, b, w);
+    if (!pl.has_sys) return;                         // no shuffles in this body
+    const size_t lane = pl.lane;
+    const int s = pl.sys, p = pl.g.p;
+    const int u = user_index(st, s);
     const int npl = st.nplan[s];
-    if (p < st.Nmax) {
-        const size_t o = ((size_t)s * st.Nmax + p) * 3;
+    for (int slot = p; slot < st.Nmax; slot += L) {
+        const size_t o = ((size_t)u * st.Nmax + slot) * 3;
+        const bool live = slot == p && slot < npl;
         if (set) {
-            if (p < npl) {
+            if (live) {
                 st.qx[lane] = io.inQ[o]; st.qy[lane] = io.inQ[o + 1]; st.qz[lane] = io.inQ[o + 2];
                 st.vx[lane] = io.inv[o]; st.vy[lane] = io.inv[o + 1]; st.vz[lane] = io.inv[o + 2];
             }
         } else {
-            const bool live = p < npl;
             io.rawQ[o] = live ? st.qx[lane] : 0.0;
             io.rawQ[o + 1] = live ? st.qy[lane] : 0.0;
             io.rawQ[o + 2] = live ? st.qz[lane] : 0.0;
@@ -581,77 +689,64 @@ __global__ void __launch_bounds__(WHG_MAX_BLOCK) k_raw(WhgState st, WhgOut io, i
     }
     if (p == 0) {
         if (set) {
-            st.nstep[s] = io.inn[s];
-            st.status[s] = io.ins[s];
+            st.nstep[s] = io.inn[u];
+            st.status[s] = io.ins[u];
         } else {
-            io.rawn[s] = st.nstep[s];
-            io.status[s] = st.status[s];
+            io.rawn[u] = st.nstep[s];
+            io.status[u] = st.status[s];
         }
     }
 }
 
 // ------------------------------------------------------------------------
-// Launchers (host side) for one G.
+// Bucket dispatch: the warp's bucket (warp-uniform), then its L instance.
 
-template <int G>
-struct Launchers {
-    static cudaError_t init(const WhgState& st, const WhgIn& in, const WhgLaunch& l)
-    {
-        k_init<G><<<l.grid, l.block, 0, l.stream>>>(st, in);
-        return cudaGetLastError();
+__device__ __forceinline__ int warp_index() { return (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); }
+
+__device__ __forceinline__ int bucket_of(const WhgBuckets& bk, int w)
+{
+    int b = 0;
+    while (b + 1 < bk.nb && w >= bk.warp0[b + 1]) ++b;
+    return b;
+}
+
+#define WHG_DISPATCH_L(Lvar, CALL)          \
+    switch (Lvar) {                         \
+    case 1: { constexpr int L_ = 1; CALL; } break; \
+    case 2: { constexpr int L_ = 2; CALL; } break; \
+    case 3: { constexpr int L_ = 3; CALL; } break; \
+    case 4: { constexpr int L_ = 4; CALL; } break; \
+    case 5: { constexpr int L_ = 5; CALL; } break; \
+    case 6: { constexpr int L_ = 6; CALL; } break; \
+    case 7: { constexpr int L_ = 7; CALL; } break; \
+    default: { constexpr int L_ = 8; CALL; } break; \
     }
 
-    template <int NT, int GRM>
-    static cudaError_t step_t(const WhgState& st, long long n, const WhgLaunch& l)
-    {
-        k_step<G, NT, GRM><<<l.grid, l.block, 0, l.stream>>>(st, n);
-        return cudaGetLastError();
-    }
+template <int NT, int GRM>
+__global__ void __launch_bounds__(WHG_MAX_BLOCK) k_step(WhgState st, WhgBuckets bk, long long n)
+{
+    const int w = warp_index();
+    if (w >= bk.warp0[bk.nb]) return;                // whole warps beyond the last bucket
+    const int b = bucket_of(bk, w);
+    WHG_DISPATCH_L(bk.L[b], (step_body<L_, NT, GRM>(st, bk, b, w, n)))
+}
 
-    static cudaError_t step(const WhgState& st, long long n, int nt, int grm, const WhgLaunch& l)
-    {
-        if (nt == 8) {
-            if (grm == 0) return step_t<8, 0>(st, n, l);
-            if (grm == 1) return step_t<8, 1>(st, n, l);
-            return step_t<8, 2>(st, n, l);
-        }
-        if (grm == 0) return step_t<6, 0>(st, n, l);
-        if (grm == 1) return step_t<6, 1>(st, n, l);
-        return step_t<6, 2>(st, n, l);
-    }
+template <int NT>
+__global__ void __launch_bounds__(WHG_MAX_BLOCK) k_read(WhgState st, WhgBuckets bk, WhgOut out)
+{
+    const int w = warp_index();
+    if (w >= bk.warp0[bk.nb]) return;
+    const int b = bucket_of(bk, w);
+    WHG_DISPATCH_L(bk.L[b], (read_body<L_, NT>(st, bk, out, b, w)))
+}
 
-    static cudaError_t read(const WhgState& st, const WhgOut& o, int nt, const WhgLaunch& l)
-    {
-        if (nt == 8)
-            k_read<G, 8><<<l.grid, l.block, 0, l.stream>>>(st, o);
-        else
-            k_read<G, 6><<<l.grid, l.block, 0, l.stream>>>(st, o);
-        return cudaGetLastError();
-    }
-
-    static cudaError_t energy(const WhgState& st, const WhgOut& o, int nt, int grm,
-                              const WhgLaunch& l)
-    {
-        if (nt == 8) {
-            if (grm == 0) k_energy<G, 8, 0><<<l.grid, l.block, 0, l.stream>>>(st, o);
-            else k_energy<G, 8, 1><<<l.grid, l.block, 0, l.stream>>>(st, o);
-        } else {
-            if (grm == 0) k_energy<G, 6, 0><<<l.grid, l.block, 0, l.stream>>>(st, o);
-            else k_energy<G, 6, 1><<<l.grid, l.block, 0, l.stream>>>(st, o);
-        }
-        return cudaGetLastError();
-    }
-
-    static cudaError_t raw(const WhgState& st, const WhgOut& o, int set, const WhgLaunch& l)
-    {
-        k_raw<G><<<l.grid, l.block, 0, l.stream>>>(st, o, set);
-        return cudaGetLastError();
-    }
-};
+template <int NT, int GRM>
+__global__ void __launch_bounds__(WHG_MAX_BLOCK) k_energy(WhgState st, WhgBuckets bk, WhgOut out)
+{
+    const int w = warp_index();
+    if (w >= bk.warp0[bk.nb]) return;
+    const int b = bucket_of(bk, w);
+    WHG_DISPATCH_L(bk.L[b], (energy_body<L_, NT, GRM>(st, bk, out, b, w)))
+}
 
 }  // namespace whg
-
-#define WHG_DEFINE_KERNEL_TABLE(G_)                                                            \
-    const WhgKernels whg_kernels_g##G_ = {whg::Launchers<G_>::init, whg::Launchers<G_>::step, \
-                                          whg::Launchers<G_>::read, whg::Launchers<G_>::energy, \
-                                          whg::Launchers<G_>::raw};

@@ -7,27 +7,43 @@
 
 // Device-resident ensemble state (structure of arrays).
 //
-// Lane arrays hold one value per (system, lane), index s * G + p, with G lanes
-// per system and lane p carrying planet p.  Lanes p >= n_planets[s] are
-// padding: mass 0, parked far from the star and never updated.  Systems
-// s >= S (up to S_pad, a multiple of the systems in one block) are padding too.
+// Systems are grouped into buckets of equal lanes-per-system L (1..8); a warp
+// of a bucket holds floor(32 / L) systems, lane p of a system carrying planet
+// p.  Lane arrays have one entry per lane of every warp (index warp * 32 +
+// lane), including lanes that hold no system and padding lanes of systems
+// with fewer than L planets: those carry mass 0, are parked far from the star
+// and are never updated.  Per-system arrays are indexed by the internal
+// system index (bucket by bucket); perm maps it to the caller's index.
 struct WhgState {
     double* m;                       // planet mass
     double *qx, *qy, *qz;            // heliocentric position Q (Sec. 3.1)
     double *vx, *vy, *vz;            // barycentric velocity v = P / m
-    double* m0;                      // [S_pad] star mass (mu = G m0, G = 1)
-    double* dt;                      // [S_pad]
-    double* M;                       // [S_pad] total mass
-    double* xcm;                     // [3][S_pad] barycentre position at t = 0
-    double* vcm;                     // [3][S_pad] barycentre velocity
-    int* nplan;                      // [S_pad] planets per system
-    int* status;                     // [S_pad] WHG_STATUS_* bits; non-zero = frozen
-    long long* nstep;                // [S_pad] completed steps (0 = synchronized)
-    int S, S_pad, Nmax;
+    double* a0;                      // initial osculating semi-major axis (stop rules)
+    double* m0;                      // [S] star mass (mu = G m0, G = 1)
+    double* dt;                      // [S]
+    double* M;                       // [S] total mass
+    double* xcm;                     // [3][S] barycentre position at t = 0
+    double* vcm;                     // [3][S] barycentre velocity
+    double* rej2;                    // [S] squared ejection distance (+inf = rule off)
+    int* nplan;                      // [S] planets per system
+    int* status;                     // [S] WHG_STATUS_* bits; non-zero = frozen
+    int* perm;                       // [S] caller's index of each internal system (null = identity)
+    long long* nstep;                // [S] completed steps (0 = synchronized)
+    int S, Nmax;
     double c_light;
+    double hill;                     // close-encounter rule: mutual Hill radii (0 = off)
+    double eject;                    // ejection rule: factor on the largest initial a (0 = off)
 };
 
-// Inertial-frame inputs (layouts of whg.h).
+// Bucket table (by value in every launch).
+struct WhgBuckets {
+    int nb;                          // number of buckets, 1..8
+    int L[8];                        // lanes per system of bucket b
+    int warp0[9];                    // first warp of bucket b; warp0[nb] = warps in use
+    int sys0[9];                     // first internal system of bucket b; sys0[nb] = S
+};
+
+// Inertial-frame inputs (layouts of whg.h), in the caller's system order.
 struct WhgIn {
     const double* masses;
     const double* pos;
@@ -57,21 +73,24 @@ struct WhgLaunch {
     cudaStream_t stream;
 };
 
-// One launcher table per lanes-per-system value G (whg_kernels_g{1,2,4,8}.cu).
-struct WhgKernels {
-    cudaError_t (*init)(const WhgState&, const WhgIn&, const WhgLaunch&);
-    cudaError_t (*step)(const WhgState&, long long nsteps, int newton_terms, int gr_mode,
-                        const WhgLaunch&);
-    cudaError_t (*read)(const WhgState&, const WhgOut&, int newton_terms, const WhgLaunch&);
-    cudaError_t (*energy)(const WhgState&, const WhgOut&, int newton_terms, int gr_mode,
-                          const WhgLaunch&);
-    cudaError_t (*raw)(const WhgState&, const WhgOut&, int set, const WhgLaunch&);
-};
+// Kernel launchers (whg_kernels_common.cu, whg_kernels_nt6.cu, whg_kernels_nt8.cu).
+cudaError_t whg_launch_init(const WhgState&, const WhgBuckets&, const WhgIn&, const WhgLaunch&);
+cudaError_t whg_launch_raw(const WhgState&, const WhgBuckets&, const WhgOut&, int set, const WhgLaunch&);
+cudaError_t whg_launch_step(const WhgState&, const WhgBuckets&, long long nsteps, int newton_terms,
+                            int gr_mode, const WhgLaunch&);
+cudaError_t whg_launch_read(const WhgState&, const WhgBuckets&, const WhgOut&, int newton_terms,
+                            const WhgLaunch&);
+cudaError_t whg_launch_energy(const WhgState&, const WhgBuckets&, const WhgOut&, int newton_terms,
+                              int gr_mode, const WhgLaunch&);
+cudaError_t whg_launch_step_nt6(const WhgState&, const WhgBuckets&, long long, int, const WhgLaunch&);
+cudaError_t whg_launch_step_nt8(const WhgState&, const WhgBuckets&, long long, int, const WhgLaunch&);
+cudaError_t whg_launch_read_nt6(const WhgState&, const WhgBuckets&, const WhgOut&, const WhgLaunch&);
+cudaError_t whg_launch_read_nt8(const WhgState&, const WhgBuckets&, const WhgOut&, const WhgLaunch&);
+cudaError_t whg_launch_energy_nt6(const WhgState&, const WhgBuckets&, const WhgOut&, int, const WhgLaunch&);
+cudaError_t whg_launch_energy_nt8(const WhgState&, const WhgBuckets&, const WhgOut&, int, const WhgLaunch&);
 
-extern const WhgKernels whg_kernels_g1;
-extern const WhgKernels whg_kernels_g2;
-extern const WhgKernels whg_kernels_g4;
-extern const WhgKernels whg_kernels_g8;
+// Lanes per system used for a bucket of n-planet systems in the packed layout.
+inline int whg_lanes_for_planets(int n) { return n == 7 ? 8 : n; }
 
 #define WHG_MAX_BLOCK 256
 

@@ -15,12 +15,12 @@
 
 namespace {
 
-// Layout of the working state for at most WHG_NOALLOC_MAX_LANES lanes
-// (systems x lanes per system, after padding to whole blocks): 7 lane arrays,
-// 9 per-system doubles, one per-system int64 and two per-system ints.
+// Layout of the working state for at most WHG_NOALLOC_MAX_LANES lanes (whole
+// warps of floor(32 / L) systems each): 8 lane arrays, 10 per-system doubles,
+// one per-system int64 and two per-system ints.
 constexpr size_t kLanes = WHG_NOALLOC_MAX_LANES;
 constexpr size_t kSystems = WHG_NOALLOC_MAX_LANES;   // at least one lane per system
-constexpr size_t kBytes = (7 * kLanes + 9 * kSystems) * sizeof(double) + kSystems * sizeof(long long) +
+constexpr size_t kBytes = (8 * kLanes + 10 * kSystems) * sizeof(double) + kSystems * sizeof(long long) +
                           2 * kSystems * sizeof(int);
 
 // Device-side scratch.  In host code this name is only a host stand-in: its
@@ -58,17 +58,6 @@ int scratch_address(void** out)
     return WHG_OK;
 }
 
-const WhgKernels* kernels_for_lanes(int G)
-{
-    switch (G) {
-    case 1: return &whg_kernels_g1;
-    case 2: return &whg_kernels_g2;
-    case 4: return &whg_kernels_g4;
-    case 8: return &whg_kernels_g8;
-    default: return nullptr;
-    }
-}
-
 }  // namespace
 
 extern "C" int whg_integrate_noalloc(int n_systems, int max_planets, const whg_options* opt_in,
@@ -88,23 +77,23 @@ extern "C" int whg_integrate_noalloc(int n_systems, int max_planets, const whg_o
     if (opt.gr_mode < 0 || opt.gr_mode > 2 || (opt.newton_terms != 6 && opt.newton_terms != 8) ||
         (opt.gr_mode && !(opt.c_light > 0.0)) || opt.steps_per_launch < 0)
         return noalloc_fail(WHG_EINVAL, "whg_integrate_noalloc: %s", "invalid options");
-    int G = opt.lanes_per_system;
-    if (G == 0) {
-        G = 1;
-        while (G < max_planets) G <<= 1;
-    }
-    const WhgKernels* kern = kernels_for_lanes(G);
-    if (!kern || G < max_planets)
-        return noalloc_fail(WHG_EINVAL, "whg_integrate_noalloc: %s", "lanes_per_system must be 1, 2, 4 or 8 and >= max_planets");
+    if (opt.lanes_per_system < 0 || opt.lanes_per_system > 8 ||
+        (opt.lanes_per_system && opt.lanes_per_system < max_planets))
+        return noalloc_fail(WHG_EINVAL, "whg_integrate_noalloc: %s", "lanes_per_system must be 0 or in max_planets..8");
+    if (opt.close_encounter_hill < 0.0 || opt.eject_factor < 0.0)
+        return noalloc_fail(WHG_EINVAL, "whg_integrate_noalloc: %s", "stop rules must be >= 0");
+    // One lane group size for every system (the planet counts stay on the
+    // device): lanes_per_system, or the packed size for max_planets.
+    const int L = opt.lanes_per_system ? opt.lanes_per_system : whg_lanes_for_planets(max_planets);
     const int block = opt.block_size ? opt.block_size : 32;
     if (block < 32 || block > WHG_MAX_BLOCK || block % 32)
         return noalloc_fail(WHG_EINVAL, "whg_integrate_noalloc: %s", "block_size must be a multiple of 32 in 32..256");
-    const long long per_block = block / G;
-    const long long S_pad = ((long long)n_systems + per_block - 1) / per_block * per_block;
-    if (S_pad * G > (long long)kLanes) {
+    const int spw = 32 / L;
+    const long long warps = ((long long)n_systems + spw - 1) / spw;
+    if (warps * 32 > (long long)kLanes) {
         char why[160];
         snprintf(why, sizeof why, "%d systems x %d lanes exceed the fixed scratch of %d lanes",
-                 n_systems, G, WHG_NOALLOC_MAX_LANES);
+                 n_systems, L, WHG_NOALLOC_MAX_LANES);
         return noalloc_fail(WHG_EINVAL, "whg_integrate_noalloc: %s", why);
     }
 
@@ -113,47 +102,56 @@ extern "C" int whg_integrate_noalloc(int n_systems, int max_planets, const whg_o
     if (rc) return rc;
 
     // Carve the state out of the scratch array (same layout as a context).
-    const size_t L = (size_t)S_pad * G, P = (size_t)S_pad;
+    const size_t NL = (size_t)warps * 32, P = (size_t)n_systems;
     WhgState st;
     double* d = (double*)base;
-    st.m = d; d += L;
-    st.qx = d; d += L;
-    st.qy = d; d += L;
-    st.qz = d; d += L;
-    st.vx = d; d += L;
-    st.vy = d; d += L;
-    st.vz = d; d += L;
+    st.m = d; d += NL;
+    st.qx = d; d += NL;
+    st.qy = d; d += NL;
+    st.qz = d; d += NL;
+    st.vx = d; d += NL;
+    st.vy = d; d += NL;
+    st.vz = d; d += NL;
+    st.a0 = d; d += NL;
     st.m0 = d; d += P;
     st.dt = d; d += P;
     st.M = d; d += P;
     st.xcm = d; d += 3 * P;
     st.vcm = d; d += 3 * P;
+    st.rej2 = d; d += P;
     long long* ll = (long long*)d;
     st.nstep = ll; ll += P;
     int* ip = (int*)ll;
     st.nplan = ip; ip += P;
     st.status = ip;
+    st.perm = nullptr;
     st.S = n_systems;
-    st.S_pad = (int)S_pad;
     st.Nmax = max_planets;
     st.c_light = opt.c_light;
+    st.hill = opt.close_encounter_hill;
+    st.eject = opt.eject_factor;
 
+    WhgBuckets bk{};
+    bk.nb = 1;
+    bk.L[0] = L;
+    bk.warp0[1] = (int)warps;
+    bk.sys0[1] = n_systems;
     WhgLaunch l;
     l.block = block;
-    l.grid = (int)(L / block);
+    l.grid = (int)((NL + block - 1) / block);
     l.stream = (cudaStream_t)cuda_stream;
 
     // The init kernel writes every lane and per-system field read later
     // (status and step counters start at zero), so stale contents left by an
     // earlier call are never read.
     WhgIn in{masses, pos, vel, n_planets, dt};
-    cudaError_t e = kern->init(st, in, l);
+    cudaError_t e = whg_launch_init(st, bk, in, l);
     if (e != cudaSuccess) return noalloc_fail(WHG_ECUDA, "init kernel: %s", cudaGetErrorString(e));
-    long long chunk = opt.steps_per_launch > 0 ? opt.steps_per_launch : 50000000LL / (long long)S_pad;
+    long long chunk = opt.steps_per_launch > 0 ? opt.steps_per_launch : 50000000LL / (warps * 4 + 1);
     if (chunk < 1) chunk = 1;
     for (long long left = n_steps; left > 0;) {
         const long long k = left < chunk ? left : chunk;
-        e = kern->step(st, k, opt.newton_terms, opt.gr_mode, l);
+        e = whg_launch_step(st, bk, k, opt.newton_terms, opt.gr_mode, l);
         if (e != cudaSuccess) return noalloc_fail(WHG_ECUDA, "step kernel: %s", cudaGetErrorString(e));
         left -= k;
     }
@@ -162,7 +160,7 @@ extern "C" int whg_integrate_noalloc(int n_systems, int max_planets, const whg_o
     o.vel = vel_out;
     o.status = status_out;
     o.t = t_out;
-    e = kern->read(st, o, opt.newton_terms, l);
+    e = whg_launch_read(st, bk, o, opt.newton_terms, l);
     if (e != cudaSuccess) return noalloc_fail(WHG_ECUDA, "read kernel: %s", cudaGetErrorString(e));
     return WHG_OK;
 }

@@ -22,6 +22,7 @@ _lib = None
 
 WHG_OK, WHG_EINVAL, WHG_ECUDA, WHG_ENOMEM, WHG_ESTATE = 0, -1, -2, -3, -4
 WHG_STATUS_NONFINITE, WHG_STATUS_HYPERBOLIC, WHG_STATUS_INVALID = 1, 2, 4
+WHG_STATUS_CLOSE_ENCOUNTER, WHG_STATUS_EJECTED = 8, 16
 WHG_MAX_PLANETS = 8
 
 
@@ -34,7 +35,8 @@ class WhgError(RuntimeError):
 class whg_options(ctypes.Structure):
     _fields_ = [("gr_mode", ctypes.c_int), ("c_light", ctypes.c_double),
                 ("newton_terms", ctypes.c_int), ("lanes_per_system", ctypes.c_int),
-                ("block_size", ctypes.c_int), ("steps_per_launch", ctypes.c_longlong)]
+                ("block_size", ctypes.c_int), ("steps_per_launch", ctypes.c_longlong),
+                ("close_encounter_hill", ctypes.c_double), ("eject_factor", ctypes.c_double)]
 
 
 def library_path() -> str:
@@ -258,7 +260,8 @@ class Integrator:
 
     def __init__(self, n_systems: int, max_planets: int, gr_mode: int = 1, c_light: float | None = None,
                  newton_terms: int = 8, lanes_per_system: int = 0, block_size: int = 0,
-                 steps_per_launch: int = 0, stream=None):
+                 steps_per_launch: int = 0, close_encounter_hill: float = 0.0,
+                 eject_factor: float = 0.0, stream=None):
         opt = whg_default_options()
         opt.gr_mode = gr_mode
         if c_light is not None:
@@ -267,6 +270,8 @@ class Integrator:
         opt.lanes_per_system = lanes_per_system
         opt.block_size = block_size
         opt.steps_per_launch = steps_per_launch
+        opt.close_encounter_hill = close_encounter_hill
+        opt.eject_factor = eject_factor
         self.S, self.N = int(n_systems), int(max_planets)
         self.stream = stream if stream is not None else current_stream()
         self.ctx = whg_create(self.S, self.N, opt, self.stream)

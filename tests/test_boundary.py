@@ -57,4 +57,5 @@ def test_options_struct_layout(lib_path):
     o = whg.whg_default_options()          # pure host function, no CUDA call
     assert o.gr_mode == 1 and o.newton_terms == 8
     assert o.c_light == pytest.approx(10065.32, rel=1e-5)
-    assert ctypes.sizeof(whg.whg_options) == 40
+    assert o.close_encounter_hill == 0.0 and o.eject_factor == 0.0
+    assert ctypes.sizeof(whg.whg_options) == 56

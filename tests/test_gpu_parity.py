@@ -346,3 +346,78 @@ def test_energy_error_statistics_match(whg, orc):
     dEo = o.energy() / E0o - 1
     assert np.abs(dEg - dEo).max() < 1e-12
     assert np.abs(dEg).max() < 1e-6
+
+
+# ------------------------------------------------------------ stop rules --
+
+def test_ejection_stop_step_matches_oracle(whg, orc):
+    """A test particle on an e = 0.9 orbit passes 1.5 a: the GPU stops it at
+    the same step as the oracle (whose step is pinned to the two-body time)."""
+    ens = inputs.test_particle(np.full(8, 1.0), np.full(8, 0.9), np.linspace(0.0, 1.0, 8), dt=0.01)
+    it = whg.Integrator(8, 1, gr_mode=0, eject_factor=1.5)
+    it.init(ens)
+    it.step(1000)
+    g = it.read_state()
+    o = orc.OracleEnsemble(8, 1, gr_mode=0, eject_factor=1.5)
+    o.init(ens)
+    o.step(1000)
+    r = o.read_state()
+    assert np.all(g[2] == whg.WHG_STATUS_EJECTED)
+    assert np.array_equal(g[2], r[2]) and np.array_equal(g[3], r[3])
+    assert np.abs(g[0] - r[0]).max() < 1e-12
+
+
+def test_close_encounter_stop_step_matches_oracle(whg, orc):
+    """Two nearly massless planets on crossing orbits (as in the oracle's pin),
+    in several phases: the same stop step as the oracle."""
+    sys_list = []
+    for k in range(6):
+        x1, v1 = inputs.elements_to_state(1.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.3 + 0.1 * k)
+        x2, v2 = inputs.elements_to_state(1.0, 1.3, 0.35, 0.0, 0.0, 0.0, 2.0)
+        sys_list.append((np.stack([x1, x2]), np.stack([v1, v2])))
+    x = np.stack([a for a, _ in sys_list])
+    v = np.stack([b for _, b in sys_list])
+    ens = inputs._assemble(1.0, np.full((6, 2), 1e-12), x, v, np.full(6, 2), np.full(6, 0.005), "")
+    it = whg.Integrator(6, 2, gr_mode=0, close_encounter_hill=2000.0)
+    it.init(ens)
+    it.step(20000)
+    g = it.read_state()
+    o = orc.OracleEnsemble(6, 2, gr_mode=0, encounter_hill=2000.0)
+    o.init(ens)
+    o.step(20000)
+    r = o.read_state()
+    assert np.all(r[2] == whg.WHG_STATUS_CLOSE_ENCOUNTER)
+    assert np.array_equal(g[2], r[2]) and np.array_equal(g[3], r[3])
+
+
+def test_stop_rules_on_compact_ensemble(whg, orc):
+    """Mixed planet counts with both stop rules on a short horizon where
+    trajectories still agree: same statuses and stop steps as the oracle."""
+    ens = inputs.compact_ensemble(12, 300)
+    kw = dict(close_encounter_hill=6.0, eject_factor=3.0)
+    g = gpu_run(whg, ens, 400, gr_mode=1, **kw)
+    o = orc.OracleEnsemble(300, 8, gr_mode=1, encounter_hill=6.0, eject_factor=3.0)
+    o.init(ens)
+    o.run_threads(400, CORES)
+    r = o.read_state() + o.get_raw() + (o.energy(),)
+    assert (r[2] == whg.WHG_STATUS_CLOSE_ENCOUNTER).sum() >= 5
+    assert_parity(g, r, 1e-10, ens.n_planets)
+
+
+def test_device_init_mixed_planet_counts(whg, orc):
+    """Device-pointer init of a mixed ensemble (the layout reads the planet
+    counts back once) matches the host-pointer path bit for bit."""
+    import torch
+    ens = inputs.compact_ensemble(13, 120)
+    a = whg.Integrator(120, 8)
+    a.init(ens)
+    a.step(300)
+    ref = a.read_state()
+    b = whg.Integrator(120, 8)
+    t = lambda x, dt=torch.float64: torch.tensor(x, dtype=dt, device="cuda")
+    whg.whg_init_device(b.ctx, t(ens.masses), t(ens.pos), t(ens.vel), t(ens.n_planets, torch.int32),
+                        t(ens.dt))
+    b.step(300)
+    out = b.read_state()
+    for u, v in zip(ref, out):
+        assert np.array_equal(u, v)

@@ -20,7 +20,8 @@ pytestmark = pytest.mark.gpu
 
 
 def _context_path(whg, ens, n):
-    it = whg.Integrator(ens.n_systems, ens.max_planets, gr_mode=1)
+    # same lane group for every system as the allocation-free call uses
+    it = whg.Integrator(ens.n_systems, ens.max_planets, gr_mode=1, lanes_per_system=8)
     it.init(ens)
     it.step(n)
     out = it.read_state()
