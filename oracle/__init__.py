@@ -22,7 +22,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liborc.so")
 _FLOPS = os.path.join(_BUILD, "orc_flopcount")
-_SOURCES = [os.path.join(_HERE, f) for f in ("orc_core.c", "orc_ensemble.c", "flopcount.cpp")]
+_TANGENT = os.path.join(_BUILD, "liborc_tangent.so")
+_SOURCES = [os.path.join(_HERE, f) for f in ("orc_core.c", "orc_ensemble.c", "flopcount.cpp",
+                                              "tangent.cpp")]
+_tlib = None
 _lock = threading.Lock()
 _lib = None
 
@@ -51,6 +54,11 @@ def build(force: bool = False) -> None:
         subprocess.check_call(["g++", "-O2", "-ffp-contract=off", "-o", tmp,
                                os.path.join(_HERE, "flopcount.cpp")])
         os.replace(tmp, _FLOPS)
+    if force or _stale(_TANGENT):
+        tmp = _TANGENT + f".{os.getpid()}.tmp"
+        subprocess.check_call(["g++", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp,
+                               os.path.join(_HERE, "tangent.cpp")])
+        os.replace(tmp, _TANGENT)
 
 
 def _load():
@@ -186,6 +194,56 @@ def stumpff(z: float, terms: int):
     c3 = np.zeros(1)
     lib.orc_stumpff(float(z), int(terms), _d(c2), _d(c3))
     return float(c2[0]), float(c3[0])
+
+
+def _load_tangent():
+    global _tlib
+    with _lock:
+        if _tlib is None:
+            build()
+            lib = ctypes.CDLL(_TANGENT)
+            D = ctypes.POINTER(ctypes.c_double)
+            lib.orc_tangent_loss.argtypes = [ctypes.c_int, D, D, D, ctypes.c_double, D, ctypes.c_longlong,
+                                             ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_int, D, D]
+            lib.orc_tangent_loss.restype = ctypes.c_int
+            _tlib = lib
+        return _tlib
+
+
+def tangent_gradient(masses, pos, vel, n_planets, dt, target, n_steps, gr_mode=1,
+                     c_light=C_LIGHT_DEFAULT, newton_terms=8):
+    """Gradient of L = sum_i |Q_i(T) - target_i|^2 (synchronized heliocentric
+    positions after n_steps) for ONE system, by forward-mode derivatives of the
+    oracle's map, one input direction per pass.  Returns (L, dL/dpos [1+n][3],
+    dL/dvel [1+n][3], dL/dmasses [1+n]) for the system's n bodies."""
+    lib = _load_tangent()
+    n = int(n_planets)
+    m = np.ascontiguousarray(masses[:1 + n], np.float64)
+    x = np.ascontiguousarray(pos[:1 + n], np.float64)
+    u = np.ascontiguousarray(vel[:1 + n], np.float64)
+    T = np.ascontiguousarray(target[:n], np.float64)
+    L = np.zeros(1)
+    dL = np.zeros(1)
+    gx = np.zeros((1 + n, 3))
+    gu = np.zeros((1 + n, 3))
+    gm = np.zeros(1 + n)
+    for kind, out in ((0, gx), (1, gu)):
+        for k in range(1 + n):
+            for c in range(3):
+                rc = lib.orc_tangent_loss(n, _d(m), _d(x), _d(u), float(dt), _d(T), int(n_steps),
+                                          int(gr_mode), float(c_light), int(newton_terms), kind, k, c,
+                                          _d(L), _d(dL))
+                if rc:
+                    raise RuntimeError("orc_tangent_loss failed (frozen system?)")
+                out[k, c] = dL[0]
+    for k in range(1 + n):
+        rc = lib.orc_tangent_loss(n, _d(m), _d(x), _d(u), float(dt), _d(T), int(n_steps), int(gr_mode),
+                                  float(c_light), int(newton_terms), 2, k, 0, _d(L), _d(dL))
+        if rc:
+            raise RuntimeError("orc_tangent_loss failed (frozen system?)")
+        gm[k] = dL[0]
+    return float(L[0]), gx, gu, gm
 
 
 def count_flops(n_planets: int, newton_terms: int = 8, gr_mode: int = 0) -> dict:

@@ -39,6 +39,7 @@ static bool operator>(Counted a, double b) { return a.v > b; }
 static bool operator<(Counted a, double b) { return a.v < b; }
 static Counted orc_sqrt(Counted x) { ++Counted::sqrts; return Counted(std::sqrt(x.v)); }
 static int orc_isfinite(Counted x) { return std::isfinite(x.v) ? 1 : 0; }
+static double orc_value(Counted x) { return x.v; }
 
 #define ORC_REAL Counted
 #include "orc_core.c"

@@ -43,7 +43,9 @@
  *     (mu = G(m_0+m_i)) of the initial state.
  *
  * This file is C99 and also compiles as C++ with ORC_REAL set to a counting
- * number type (oracle/flopcount.cpp); that build only counts operations.
+ * number type (oracle/flopcount.cpp; it only counts operations) or, together
+ * with ORC_MASS, to a dual number (oracle/tangent.cpp: forward-mode
+ * derivatives of the same map).
  */
 #ifndef ORC_CORE_C
 #define ORC_CORE_C
@@ -55,8 +57,14 @@
 #define ORC_REAL double
 static double orc_sqrt(double x) { return sqrt(x); }
 static int orc_isfinite(double x) { return isfinite(x) != 0; }
+static double orc_value(double x) { return x; }
+#endif
+#ifndef ORC_MASS
+#define ORC_MASS double          /* masses: double, or the tangent type in tangent.cpp */
+static double orc_mass_value(double x) { return x; }
 #endif
 typedef ORC_REAL orc_real;
+typedef ORC_MASS orc_mass;
 
 #define ORC_NMAX 8            /* planets per system */
 #define ORC_TMAX 12           /* longest Stumpff series supported */
@@ -82,13 +90,13 @@ typedef struct {
  * velocity relative to the barycentre; Xcm, Vcm, M describe H_0. */
 typedef struct {
     int n;                      /* number of planets, 1..ORC_NMAX */
-    double m0;                  /* star mass */
-    double m[ORC_NMAX];
+    orc_mass m0;                /* star mass */
+    orc_mass m[ORC_NMAX];
     orc_real Q[ORC_NMAX][3];
     orc_real v[ORC_NMAX][3];
     double dt;
-    double M;                   /* total mass */
-    double Xcm[3], Vcm[3];      /* barycentre position (at t = 0) and velocity */
+    orc_mass M;                 /* total mass */
+    orc_real Xcm[3], Vcm[3];    /* barycentre position (at t = 0) and velocity */
     long long nstep;            /* completed steps; 0 = synchronized state */
     int status;
     double a0[ORC_NMAX];        /* osculating heliocentric semi-major axes at init (stop rules) */
@@ -138,7 +146,7 @@ static void orc_stiefel(orc_real beta, orc_real X, int terms, orc_real G[4])
  * (Sec. 3.2, Eq. 3) for time h with mu = G m_0 (G = 1).  Universal variable X,
  * Kepler function F(X) = r_0 G_1 + eta_0 G_2 + mu G_3 - h, F' = r, F'' = dr/dX.
  * Fixed iteration count, no convergence test, no branches.  Writes beta. */
-static void orc_kepler_drift(double mu, double h, orc_real Q[3], orc_real v[3],
+static void orc_kepler_drift(orc_mass mu, double h, orc_real Q[3], orc_real v[3],
                              const orc_options* opt, orc_real* beta_out)
 {
     orc_real r0 = orc_sqrt(Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2]);
@@ -220,7 +228,8 @@ static int orc_interaction(orc_system* s, double h, const orc_options* opt)
             r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
             if (opt->encounter_hill > 0.0) {
                 /* mutual Hill radius from the initial semi-major axes */
-                double rh = opt->encounter_hill * cbrt((s->m[i] + s->m[j]) / (3.0 * s->m0)) *
+                double rh = opt->encounter_hill *
+                            cbrt(orc_mass_value(s->m[i] + s->m[j]) / (3.0 * orc_mass_value(s->m0))) *
                             0.5 * (s->a0[i] + s->a0[j]);
                 if (r2 < rh * rh) close = 1;
             }
@@ -241,7 +250,7 @@ static int orc_interaction(orc_system* s, double h, const orc_options* opt)
 /* Acceleration from the 1/r^2 potential centred on the star (Sec. 3.3, GR
  * paragraph; Nobili & Roxburgh 1986): Phi = -3 (G m_0)^2 / (c^2 r^2) per unit
  * planet mass, a_GR(Q) = -grad Phi = -6 (G m_0)^2 Q / (c^2 |Q|^4). */
-static void orc_gr_acc(double m0, double c_light, const orc_real Q[3], orc_real a[3])
+static void orc_gr_acc(orc_mass m0, double c_light, const orc_real Q[3], orc_real a[3])
 {
     orc_real r2 = Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2];
     orc_real k = -6.0 * m0 * m0 / (c_light * c_light) / (r2 * r2);
@@ -334,6 +343,49 @@ static void orc_synchronize(const orc_system* s, orc_system* out, const orc_opti
             orc_kepler_drift(s->m0, 0.5 * s->dt, out->Q[i], out->v[i], opt, &beta);
         }
     }
+}
+
+/* Inertial -> democratic heliocentric (Sec. 3.1): Q_i = x_i - x_0 and
+ * v_i = u_i - V_cm (so P_i = m_i v_i is measured from the barycentre);
+ * M, X_cm and V_cm are kept for H_0 and for the way back.  m [1+n],
+ * x, u [1+n][3], body 0 the star. */
+static void orc_to_dh(orc_system* s, int n, const orc_mass* m, const orc_real* x, const orc_real* u,
+                      double dt)
+{
+    int k, i, c;
+    s->n = n;
+    s->m0 = m[0];
+    s->dt = dt;
+    s->M = 0.0;
+    for (k = 0; k <= n; ++k) s->M = s->M + m[k];
+    for (c = 0; c < 3; ++c) {
+        orc_real px = 0.0, pu = 0.0;
+        for (k = 0; k <= n; ++k) {
+            px = px + m[k] * x[3 * k + c];
+            pu = pu + m[k] * u[3 * k + c];
+        }
+        s->Xcm[c] = px / s->M;
+        s->Vcm[c] = pu / s->M;
+    }
+    for (i = 0; i < n; ++i) {
+        double r2 = 0.0, w2 = 0.0;
+        s->m[i] = m[1 + i];
+        for (c = 0; c < 3; ++c) {
+            s->Q[i][c] = x[3 * (1 + i) + c] - x[c];
+            s->v[i][c] = u[3 * (1 + i) + c] - s->Vcm[c];
+        }
+        for (c = 0; c < 3; ++c) {
+            double dx = orc_value(x[3 * (1 + i) + c]) - orc_value(x[c]);
+            double du = orc_value(u[3 * (1 + i) + c]) - orc_value(u[c]);
+            r2 += dx * dx;
+            w2 += du * du;
+        }
+        /* heliocentric two-body osculating semi-major axis, mu = G (m_0 + m_i),
+         * for the stop rules only (no derivative needed) */
+        s->a0[i] = 1.0 / (2.0 / sqrt(r2) - w2 / (orc_mass_value(m[0]) + orc_mass_value(m[1 + i])));
+    }
+    s->nstep = 0;
+    s->status = 0;
 }
 
 #endif /* ORC_CORE_C */

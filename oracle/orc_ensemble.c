@@ -56,44 +56,6 @@ void orc_destroy(orc_ensemble* e)
     free(e);
 }
 
-/* Inertial -> democratic heliocentric (Sec. 3.1): Q_i = x_i - x_0 and
- * v_i = u_i - V_cm (so P_i = m_i v_i is measured from the barycentre);
- * M, X_cm and V_cm are kept for H_0 and for the way back. */
-static void orc_to_dh(orc_system* s, int n, const double* m, const double* x, const double* u,
-                      double dt)
-{
-    int k, i, c;
-    s->n = n;
-    s->m0 = m[0];
-    s->dt = dt;
-    s->M = 0.0;
-    for (k = 0; k <= n; ++k) s->M += m[k];
-    for (c = 0; c < 3; ++c) {
-        double px = 0.0, pu = 0.0;
-        for (k = 0; k <= n; ++k) {
-            px += m[k] * x[3 * k + c];
-            pu += m[k] * u[3 * k + c];
-        }
-        s->Xcm[c] = px / s->M;
-        s->Vcm[c] = pu / s->M;
-    }
-    for (i = 0; i < n; ++i) {
-        double r2 = 0.0, w2 = 0.0;
-        s->m[i] = m[1 + i];
-        for (c = 0; c < 3; ++c) {
-            double dx = x[3 * (1 + i) + c] - x[c], du = u[3 * (1 + i) + c] - u[c];
-            s->Q[i][c] = dx;
-            s->v[i][c] = u[3 * (1 + i) + c] - s->Vcm[c];
-            r2 += dx * dx;
-            w2 += du * du;
-        }
-        /* heliocentric two-body osculating semi-major axis, mu = G (m_0 + m_i) */
-        s->a0[i] = 1.0 / (2.0 / sqrt(r2) - w2 / (m[0] + m[1 + i]));
-    }
-    s->nstep = 0;
-    s->status = 0;
-}
-
 /* Democratic heliocentric -> inertial at time t = nstep * dt:
  * x_0 = X_cm + V_cm t - sum m_i Q_i / M, x_i = x_0 + Q_i,
  * u_0 = V_cm - sum m_i v_i / m_0, u_i = v_i + V_cm. */
