@@ -212,6 +212,54 @@ def oracle_rate(ens, gr_mode: int, target_cpu_seconds: float, threads: int):
     return S * n / dt, f"{S} systems x {n} steps on {used} threads ({dt:.1f} s wall)", used
 
 
+def measure_adjoint(whg, torch, systems=1024, steps=10000, every=100, seed=4242):
+    """Cost of the adjoint on the gradient workload: 1024 Solar-System-shaped
+    systems, 1e4 steps, checkpoints every 100 steps, loss on the final
+    heliocentric positions.  Returns CUDA-event times of a plain forward
+    (whg_step), the checkpointed forward and the backward (adjoint kernels)."""
+    ens = inputs.solar_ensemble(seed, systems)
+    rng = np.random.default_rng(seed)
+    T = ens.pos[:, 1:] - ens.pos[:, :1] + rng.normal(0, 0.05, ens.pos[:, 1:].shape)
+    dev = lambda a, dt=torch.float64: torch.tensor(a, dtype=dt, device="cuda")
+    stream = torch.cuda.Stream()
+    res = {}
+    with torch.cuda.stream(stream):
+        m, x, u, npl, dt, tgt = (dev(ens.masses), dev(ens.pos), dev(ens.vel), dev(ens.n_planets, torch.int32),
+                                 dev(ens.dt), dev(T))
+        loss = torch.empty(systems, dtype=torch.float64, device="cuda")
+        gx = torch.empty_like(x)
+        gu = torch.empty_like(x)
+        gm = torch.empty_like(m)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        for rep in range(2):                          # first round warms up
+            a = whg.Integrator(systems, 8, gr_mode=1, stream=stream.cuda_stream)
+            b = whg.Integrator(systems, 8, gr_mode=1, stream=stream.cuda_stream)
+            whg.whg_init_device(a.ctx, m, x, u, npl, dt)
+            whg.whg_init_device(b.ctx, m, x, u, npl, dt)
+            stream.synchronize()
+            ev[0].record(stream)
+            a.step(steps)
+            ev[1].record(stream)
+            whg.whg_adjoint_forward(b.ctx, steps, every, tgt, loss)
+            ev[2].record(stream)
+            whg.whg_adjoint_backward(b.ctx, None, gx, gu, gm)
+            ev[3].record(stream)
+            stream.synchronize()
+            a.close()
+            b.close()
+        fwd = ev[0].elapsed_time(ev[1])
+        afw = ev[1].elapsed_time(ev[2])
+        bwd = ev[2].elapsed_time(ev[3])
+    res = {"workload": f"{systems} Solar-System-shaped systems, {steps} steps, checkpoint every {every}, "
+                       "loss = sum |Q_i(T) - target_i|^2",
+           "forward_ms": round(fwd, 3), "adjoint_forward_ms": round(afw, 3),
+           "adjoint_backward_ms": round(bwd, 3),
+           "backward_over_forward": round(bwd / fwd, 3),
+           "gradient_over_forward": round((afw + bwd) / fwd, 3),
+           "finite_gradients": bool(torch.isfinite(gx).all().item() and torch.isfinite(gm).all().item())}
+    return res
+
+
 # ------------------------------------------------------------ GPU arm --
 
 def run_whg(args):
@@ -305,6 +353,7 @@ def run_whg(args):
     kernel_ms = total_ms / args.steps / max(launches_per_step, 1.0)
     achieved = flops * S * (chunk / max(launches_per_step, 1.0)) / (kernel_ms / 1e3) / 1e12
     dfma = whg.whg_measure_fp64_tflops(0.5)
+    adjoint = measure_adjoint(whg, torch) if world == 1 else None
     roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                 "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
                 "traffic": profiled_traffic(),
@@ -323,6 +372,7 @@ def run_whg(args):
                     "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps,
                     "api": "whg_init(host) + whg_step + whg_read_state(host)"},
             "gpu_launches": int(launches),
+            "adjoint": adjoint,
             "clocks": clock_info,
             "systems_flagged": bad}
     it.close()

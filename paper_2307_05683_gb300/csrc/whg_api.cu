@@ -29,6 +29,16 @@ struct whg_ctx {
     double* stage_d;          // S * (7 * (1 + Nmax) + 1) doubles
     int* stage_i;             // 2 * S ints
     long long* stage_l;       // S int64
+    long long host_nstep;     // steps since init (-1: unknown after set_raw)
+    // adjoint buffers (allocated by whg_adjoint_forward, kept until destroy)
+    double* adj_buf;
+    size_t adj_bytes;
+    WhgAdj adj;
+    long long adj_n;
+    int adj_K, adj_nseg;
+    bool adj_ready;
+    cudaStream_t side;        // second stream for tape recomputation (created on first use)
+    cudaEvent_t ev_tape[2], ev_back[2], ev_entry;
     char err[256];
 };
 
@@ -312,6 +322,8 @@ static int init_common(whg_ctx* c, const WhgIn& in, const int* nplan_host)
     int rc = launch_check(c, whg_launch_init(c->st, c->bk, in, launch_cfg(c)), "init kernel");
     if (rc) return rc;
     c->initialized = true;
+    c->host_nstep = 0;
+    c->adj_ready = false;
     WHG_CUDA(c, cudaStreamSynchronize(c->stream));      // host buffers may be reused on return
     return WHG_OK;
 }
@@ -370,6 +382,8 @@ int whg_step(whg_ctx* c, long long n)
         if (chunk < 1) chunk = 1;
     }
     WhgLaunch l = launch_cfg(c);
+    if (c->host_nstep >= 0) c->host_nstep += n;
+    c->adj_ready = false;
     while (n > 0) {
         const long long k = n < chunk ? n : chunk;
         int rc = launch_check(c, whg_launch_step(c->st, c->bk, k, c->opt.newton_terms, c->opt.gr_mode, l),
@@ -480,6 +494,8 @@ int whg_set_raw(whg_ctx* c, const double* Q, const double* v, const long long* n
     o.ins = c->stage_i;
     int rc = launch_check(c, whg_launch_raw(c->st, c->bk, o, 1, launch_cfg(c)), "raw kernel");
     if (rc) return rc;
+    c->host_nstep = -1;
+    c->adj_ready = false;
     WHG_CUDA(c, cudaStreamSynchronize(c->stream));
     return WHG_OK;
 }
@@ -495,12 +511,141 @@ long long whg_launch_count(const whg_ctx* c) { return c ? c->launches : 0; }
 
 const char* whg_last_error(const whg_ctx* c) { return c ? c->err : g_create_err; }
 
+int whg_adjoint_forward(whg_ctx* c, long long n_steps, int checkpoint_every, const double* target,
+                        double* loss)
+{
+    if (!c) return WHG_EINVAL;
+    if (!c->initialized || c->host_nstep != 0)
+        return fail(c, WHG_ESTATE, "whg_adjoint_forward needs a freshly initialised context (no steps yet)");
+    if (n_steps < 0 || checkpoint_every < 1)
+        return fail(c, WHG_EINVAL, "need n_steps >= 0 and checkpoint_every >= 1");
+    if (!target || !loss) return fail(c, WHG_EINVAL, "null target or loss");
+    const size_t NL = (size_t)c->bk.warp0[c->bk.nb] * 32;
+    const long long nseg = (n_steps + checkpoint_every - 1) / checkpoint_every;
+    const int K = (int)(n_steps < checkpoint_every ? (n_steps > 0 ? n_steps : 1) : checkpoint_every);
+    const size_t tgt = (size_t)c->S * c->Nmax * 3;
+    const size_t nd = (size_t)(nseg + 1) * 6 * NL + 2 * (size_t)K * 16 * NL + 8 * NL + tgt;
+    const size_t bytes = nd * sizeof(double);
+    if (bytes > c->adj_bytes) {
+        if (c->adj_buf) cudaFree(c->adj_buf);
+        c->adj_buf = nullptr;
+        c->adj_bytes = 0;
+        cudaError_t e = cudaMalloc(&c->adj_buf, bytes);
+        if (e != cudaSuccess) return fail(c, WHG_ENOMEM, "cudaMalloc(%zu) for the adjoint: %s", bytes,
+                                          cudaGetErrorString(e));
+        c->adj_bytes = bytes;
+    }
+    WhgAdj& a = c->adj;
+    a = WhgAdj{};
+    a.NL = NL;
+    a.ckpt = c->adj_buf;
+    a.tape = a.ckpt + (size_t)(nseg + 1) * 6 * NL;
+    a.tape_len = (size_t)K * 16 * NL;
+    a.lam = a.tape + 2 * a.tape_len;
+    double* tcopy = a.lam + 8 * NL;
+    a.target = tcopy;
+    WHG_CUDA(c, cudaMemcpyAsync(tcopy, target, tgt * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    const WhgLaunch l = launch_cfg(c);
+    for (long long seg = 0; seg < nseg; ++seg) {
+        int rc = launch_check(c, whg_launch_adj_save(c->st, c->bk, a, (int)seg, l), "checkpoint kernel");
+        if (rc) return rc;
+        const long long k = (seg + 1) * checkpoint_every <= n_steps ? checkpoint_every
+                                                                     : n_steps - seg * checkpoint_every;
+        rc = whg_step(c, k);
+        if (rc) return rc;
+    }
+    int rc = launch_check(c, whg_launch_adj_save(c->st, c->bk, a, (int)nseg, l), "checkpoint kernel");
+    if (rc) return rc;
+    a.loss = loss;
+    rc = launch_check(c, whg_launch_adj_loss(c->st, c->bk, a, 0, c->opt.newton_terms, l), "loss kernel");
+    if (rc) return rc;
+    c->adj_n = n_steps;
+    c->adj_K = checkpoint_every;
+    c->adj_nseg = (int)nseg;
+    c->adj_ready = true;
+    return WHG_OK;
+}
+
+int whg_adjoint_backward(whg_ctx* c, const double* loss_weight, double* grad_pos, double* grad_vel,
+                         double* grad_mass)
+{
+    if (!c) return WHG_EINVAL;
+    if (!c->adj_ready)
+        return fail(c, WHG_ESTATE, "whg_adjoint_backward needs whg_adjoint_forward first (and no steps since)");
+    WhgAdj a = c->adj;
+    a.weight = loss_weight;
+    a.gx = grad_pos;
+    a.gu = grad_vel;
+    a.gm = grad_mass;
+    a.loss = nullptr;
+    const WhgLaunch l = launch_cfg(c);
+    int rc = launch_check(c, whg_launch_adj_loss(c->st, c->bk, a, 1, c->opt.newton_terms, l), "adjoint start");
+    if (rc) return rc;
+    if (!c->side) {
+        WHG_CUDA(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; ++i) {
+            WHG_CUDA(c, cudaEventCreateWithFlags(&c->ev_tape[i], cudaEventDisableTiming));
+            WHG_CUDA(c, cudaEventCreateWithFlags(&c->ev_back[i], cudaEventDisableTiming));
+        }
+        WHG_CUDA(c, cudaEventCreateWithFlags(&c->ev_entry, cudaEventDisableTiming));
+    }
+    // the side stream starts after everything issued so far (checkpoints, adjoint start)
+    WHG_CUDA(c, cudaEventRecord(c->ev_entry, c->stream));
+    WHG_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_entry, 0));
+    // Segment s's products run on the context's stream while the tape of
+    // segment s-1 is recomputed on the side stream into the other buffer,
+    // once the products of segment s+1 are done with that buffer.
+    WhgLaunch side = l;
+    side.stream = c->side;
+    const int K = c->adj_K, nseg = c->adj_nseg;
+    auto seg_len = [&](int seg) {
+        const long long s0 = (long long)seg * K;
+        return (int)(s0 + K <= c->adj_n ? K : c->adj_n - s0);
+    };
+    if (nseg > 0) {
+        rc = launch_check(c, whg_launch_adj_tape(c->st, c->bk, a, nseg - 1, (long long)(nseg - 1) * K,
+                                                 seg_len(nseg - 1), (nseg - 1) & 1, c->opt.newton_terms,
+                                                 c->opt.gr_mode, l),
+                          "adjoint tape kernel");
+        if (rc) return rc;
+    }
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+        if (seg >= 1) {
+            const int buf = (seg - 1) & 1;
+            if (seg + 1 <= nseg - 1) WHG_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_back[buf], 0));
+            rc = launch_check(c, whg_launch_adj_tape(c->st, c->bk, a, seg - 1, (long long)(seg - 1) * K,
+                                                     seg_len(seg - 1), buf, c->opt.newton_terms,
+                                                     c->opt.gr_mode, side),
+                              "adjoint tape kernel");
+            if (rc) return rc;
+            WHG_CUDA(c, cudaEventRecord(c->ev_tape[buf], c->side));
+        }
+        if (seg < nseg - 1) WHG_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_tape[seg & 1], 0));
+        rc = launch_check(c, whg_launch_adj_back(c->st, c->bk, a, (long long)seg * K, seg_len(seg), seg & 1,
+                                                 c->opt.newton_terms, c->opt.gr_mode, l),
+                          "adjoint back kernel");
+        if (rc) return rc;
+        WHG_CUDA(c, cudaEventRecord(c->ev_back[seg & 1], c->stream));
+    }
+    return launch_check(c, whg_launch_adj_finish(c->st, c->bk, a, l), "adjoint finish kernel");
+}
+
 void whg_destroy(whg_ctx* c)
 {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     cudaFree(c->st.m);
     cudaFree(c->stage_d);
+    if (c->adj_buf) cudaFree(c->adj_buf);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        for (int i = 0; i < 2; ++i) {
+            cudaEventDestroy(c->ev_tape[i]);
+            cudaEventDestroy(c->ev_back[i]);
+        }
+        cudaEventDestroy(c->ev_entry);
+        cudaStreamDestroy(c->side);
+    }
     delete c;
 }
 

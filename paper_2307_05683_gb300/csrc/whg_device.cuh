@@ -169,10 +169,11 @@ __device__ __forceinline__ void stumpff_c2c3(double z, double& c2, double& c3)
 // values at the last Newton point X1 by one Taylor step (dG_n/dX = G_{n-1});
 // |d| is the last Newton correction, so the neglected d^2 terms are far below
 // rounding.  Then the Lagrange f - 1, g, fdot, gdot - 1.  No branches.
-// Returns beta > 0.
+// Returns beta > 0; Xout receives the final universal variable.
 template <int NT>
 __device__ __forceinline__ bool kepler_drift(double mu, double h, double& qx, double& qy,
-                                             double& qz, double& vx, double& vy, double& vz)
+                                             double& qz, double& vx, double& vy, double& vz,
+                                             double& Xout)
 {
     const double r0sq = fma(qx, qx, fma(qy, qy, qz * qz));
     const double r0i = rsqrt(r0sq);
@@ -230,7 +231,16 @@ __device__ __forceinline__ bool kepler_drift(double mu, double h, double& qx, do
     vy = fma(fd, qy, fma(gdm1, vy, vy));
     vz = fma(fd, qz, fma(gdm1, vz, vz));
     qx = nqx; qy = nqy; qz = nqz;
+    Xout = Xf;
     return beta > 0.0;
+}
+
+template <int NT>
+__device__ __forceinline__ bool kepler_drift(double mu, double h, double& qx, double& qy,
+                                             double& qz, double& vx, double& vy, double& vz)
+{
+    double X;
+    return kepler_drift<NT>(mu, h, qx, qy, qz, vx, vy, vz, X);
 }
 
 // ------------------------------------------------------------------------

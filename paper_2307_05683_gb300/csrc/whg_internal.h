@@ -68,6 +68,21 @@ struct WhgOut {
     const int* ins;
 };
 
+// Buffers of the adjoint (reverse-mode) pass; NL = lanes of the layout.
+struct WhgAdj {
+    double* ckpt;                    // [nseg + 1][6][NL] state every K steps
+    double* tape;                    // [2][K][16][NL] per-step values of one segment (two buffers)
+    size_t tape_len;                 // K * 16 * NL (one buffer)
+    double* lam;                     // [8][NL] adjoints: Q (3), v (3), m, m0 (partial)
+    const double* target;            // [S][Nmax][3] caller order
+    double* loss;                    // [S] caller order
+    const double* weight;            // [S] dTotal/dL_s (null = 1)
+    double* gx;                      // [S][1+Nmax][3] gradients, caller layout
+    double* gu;
+    double* gm;                      // [S][1+Nmax]
+    size_t NL;
+};
+
 struct WhgLaunch {
     int grid, block;
     cudaStream_t stream;
@@ -88,6 +103,15 @@ cudaError_t whg_launch_read_nt6(const WhgState&, const WhgBuckets&, const WhgOut
 cudaError_t whg_launch_read_nt8(const WhgState&, const WhgBuckets&, const WhgOut&, const WhgLaunch&);
 cudaError_t whg_launch_energy_nt6(const WhgState&, const WhgBuckets&, const WhgOut&, int, const WhgLaunch&);
 cudaError_t whg_launch_energy_nt8(const WhgState&, const WhgBuckets&, const WhgOut&, int, const WhgLaunch&);
+
+cudaError_t whg_launch_adj_save(const WhgState&, const WhgBuckets&, const WhgAdj&, int slot, const WhgLaunch&);
+cudaError_t whg_launch_adj_loss(const WhgState&, const WhgBuckets&, const WhgAdj&, int start, int newton_terms,
+                                const WhgLaunch&);
+cudaError_t whg_launch_adj_tape(const WhgState&, const WhgBuckets&, const WhgAdj&, int seg, long long s0,
+                                int nk, int buf, int newton_terms, int gr_mode, const WhgLaunch&);
+cudaError_t whg_launch_adj_back(const WhgState&, const WhgBuckets&, const WhgAdj&, long long s0, int nk,
+                                int buf, int newton_terms, int gr_mode, const WhgLaunch&);
+cudaError_t whg_launch_adj_finish(const WhgState&, const WhgBuckets&, const WhgAdj&, const WhgLaunch&);
 
 // Lanes per system used for a bucket of n-planet systems in the packed layout.
 inline int whg_lanes_for_planets(int n) { return n == 7 ? 8 : n; }

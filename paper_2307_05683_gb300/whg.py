@@ -75,6 +75,8 @@ def load():
             "whg_destroy": (None, [P]),
             "whg_measure_fp64_tflops": (ctypes.c_int, [ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
             "whg_test_special": (ctypes.c_int, [D, ctypes.c_int, D]),
+            "whg_adjoint_forward": (ctypes.c_int, [P, ctypes.c_longlong, ctypes.c_int, D, D]),
+            "whg_adjoint_backward": (ctypes.c_int, [P, D, D, D, D]),
             "whg_integrate_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int,
                                                      ctypes.POINTER(whg_options), D, D, D, I, D,
                                                      ctypes.c_longlong, D, D, I, D, ctypes.c_void_p]),
@@ -93,7 +95,8 @@ def exported_symbols() -> list[str]:
             "whg_step", "whg_read_state", "whg_read_state_device", "whg_energy",
             "whg_energy_device", "whg_get_raw", "whg_set_raw", "whg_synchronize",
             "whg_launch_count", "whg_last_error", "whg_destroy", "whg_measure_fp64_tflops",
-            "whg_test_special", "whg_integrate_noalloc"]
+            "whg_test_special", "whg_integrate_noalloc", "whg_adjoint_forward",
+            "whg_adjoint_backward"]
 
 
 def _check(ctx, rc: int) -> None:
@@ -206,6 +209,17 @@ def whg_set_raw(ctx, Q, v, nstep, status) -> None:
     n, pn = _host(nstep, np.int64)
     s, ps = _host(status, np.int32)
     _check(ctx, load().whg_set_raw(ctx, pq, pv, pn, ps))
+
+
+def whg_adjoint_forward(ctx, n_steps: int, checkpoint_every: int, target, loss) -> None:
+    _check(ctx, load().whg_adjoint_forward(ctx, int(n_steps), int(checkpoint_every),
+                                           _dev(target, "torch.float64"), _dev(loss, "torch.float64")))
+
+
+def whg_adjoint_backward(ctx, loss_weight, grad_pos, grad_vel, grad_mass) -> None:
+    _check(ctx, load().whg_adjoint_backward(ctx, _dev(loss_weight, "torch.float64"),
+                                            _dev(grad_pos, "torch.float64"), _dev(grad_vel, "torch.float64"),
+                                            _dev(grad_mass, "torch.float64")))
 
 
 def whg_synchronize(ctx) -> None:
