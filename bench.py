@@ -260,6 +260,32 @@ def measure_adjoint(whg, torch, systems=1024, steps=10000, every=100, seed=4242)
     return res
 
 
+def throughput_sweep(whg, torch, sizes=tuple(1 << k for k in range(14, 21)), window_s=0.4, seed=77):
+    """System-steps/s and FP64 fraction against ensemble size (Solar-System-
+    shaped systems, GR on, default launch configuration), each point timed
+    with CUDA events over a window of about window_s after a warm-up call."""
+    base = inputs.solar_ensemble(seed, 4096)
+    out = []
+    stream = torch.cuda.Stream()
+    for S in sizes:
+        ens = base.tile(S)
+        it = whg.Integrator(S, 8, gr_mode=1, stream=stream.cuda_stream)
+        it.init(ens)
+        n = max(32, int(2.4e8 * window_s / S))
+        it.step(n)
+        it.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it.step(n)
+        e1.record(stream)
+        e1.synchronize()
+        rate = S * n / (e0.elapsed_time(e1) / 1e3)
+        it.close()
+        out.append({"systems": S, "steps": n, "system_steps_per_s": round(rate, 1),
+                    "frac": round(rate * ALG_FLOPS[(8, 8, 1)] / 1e12 / FP64_PEAK_TFLOPS, 4)})
+    return out
+
+
 # ------------------------------------------------------------ GPU arm --
 
 def run_whg(args):
@@ -354,6 +380,7 @@ def run_whg(args):
     achieved = flops * S * (chunk / max(launches_per_step, 1.0)) / (kernel_ms / 1e3) / 1e12
     dfma = whg.whg_measure_fp64_tflops(0.5)
     adjoint = measure_adjoint(whg, torch) if world == 1 else None
+    sweep = throughput_sweep(whg, torch) if world == 1 else None
     roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                 "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
                 "traffic": profiled_traffic(),
@@ -373,6 +400,7 @@ def run_whg(args):
                     "api": "whg_init(host) + whg_step + whg_read_state(host)"},
             "gpu_launches": int(launches),
             "adjoint": adjoint,
+            "sweep": sweep,
             "clocks": clock_info,
             "systems_flagged": bad}
     it.close()

@@ -89,6 +89,10 @@ typedef struct {
     double eject_factor;      /* ensemble stop rule, 0 = off: stop a system when a planet
                                  is farther from the star than this factor times the
                                  system's largest initial a at the start of a step */
+    int graph_launches;       /* 0 = off; else whg_step replays a CUDA graph of this many
+                                 step launches (captured once per init and launch length)
+                                 for the whole multiples, and launches the rest directly.
+                                 Results are bitwise those of direct launches. */
 } whg_options;
 
 /* Fill *opt with the defaults above. */

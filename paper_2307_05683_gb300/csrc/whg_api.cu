@@ -39,6 +39,10 @@ struct whg_ctx {
     bool adj_ready;
     cudaStream_t side;        // second stream for tape recomputation (created on first use)
     cudaEvent_t ev_tape[2], ev_back[2], ev_entry;
+    // CUDA graph of graph_launches step launches of graph_chunk steps each
+    cudaStream_t capture;
+    cudaGraphExec_t graph;
+    long long graph_chunk;
     char err[256];
 };
 
@@ -194,6 +198,7 @@ void whg_default_options(whg_options* opt)
     opt->steps_per_launch = 0;
     opt->close_encounter_hill = 0.0;
     opt->eject_factor = 0.0;
+    opt->graph_launches = 0;
 }
 
 int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options* opt_in,
@@ -225,6 +230,8 @@ int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options*
                     WHG_MAX_BLOCK);
     if (opt.steps_per_launch < 0)
         return fail(nullptr, WHG_EINVAL, "steps_per_launch=%lld must be >= 0", opt.steps_per_launch);
+    if (opt.graph_launches < 0 || opt.graph_launches > 4096)
+        return fail(nullptr, WHG_EINVAL, "graph_launches=%d must be in 0..4096", opt.graph_launches);
 
     whg_ctx* c = new (std::nothrow) whg_ctx();
     if (!c) return fail(nullptr, WHG_ENOMEM, "host allocation failed");
@@ -324,6 +331,10 @@ static int init_common(whg_ctx* c, const WhgIn& in, const int* nplan_host)
     c->initialized = true;
     c->host_nstep = 0;
     c->adj_ready = false;
+    if (c->graph) {                                      // kernel arguments changed: capture again
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
     WHG_CUDA(c, cudaStreamSynchronize(c->stream));      // host buffers may be reused on return
     return WHG_OK;
 }
@@ -384,6 +395,38 @@ int whg_step(whg_ctx* c, long long n)
     WhgLaunch l = launch_cfg(c);
     if (c->host_nstep >= 0) c->host_nstep += n;
     c->adj_ready = false;
+    const long long G = c->opt.graph_launches;
+    if (G > 0 && n >= G * chunk) {
+        if (!c->graph || c->graph_chunk != chunk) {      // capture G launches once
+            if (c->graph) {
+                cudaGraphExecDestroy(c->graph);
+                c->graph = nullptr;
+            }
+            if (!c->capture) WHG_CUDA(c, cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking));
+            WhgLaunch cl = l;
+            cl.stream = c->capture;
+            WHG_CUDA(c, cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaSuccess;
+            for (long long i = 0; i < G && e == cudaSuccess; ++i)
+                e = whg_launch_step(c->st, c->bk, chunk, c->opt.newton_terms, c->opt.gr_mode, cl);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(c->capture, &graph);
+            if (e != cudaSuccess) return cuda_fail(c, e, "step kernel (capture)");
+            if (e2 != cudaSuccess) return cuda_fail(c, e2, "cudaStreamEndCapture");
+            const cudaError_t e3 = cudaGraphInstantiate(&c->graph, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e3 != cudaSuccess) {
+                c->graph = nullptr;
+                return cuda_fail(c, e3, "cudaGraphInstantiate");
+            }
+            c->graph_chunk = chunk;
+        }
+        while (n >= G * chunk) {                          // replay on the context's stream
+            WHG_CUDA(c, cudaGraphLaunch(c->graph, c->stream));
+            c->launches += G;
+            n -= G * chunk;
+        }
+    }
     while (n > 0) {
         const long long k = n < chunk ? n : chunk;
         int rc = launch_check(c, whg_launch_step(c->st, c->bk, k, c->opt.newton_terms, c->opt.gr_mode, l),
@@ -646,6 +689,8 @@ void whg_destroy(whg_ctx* c)
         cudaEventDestroy(c->ev_entry);
         cudaStreamDestroy(c->side);
     }
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->capture) cudaStreamDestroy(c->capture);
     delete c;
 }
 

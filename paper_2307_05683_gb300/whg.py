@@ -36,7 +36,8 @@ class whg_options(ctypes.Structure):
     _fields_ = [("gr_mode", ctypes.c_int), ("c_light", ctypes.c_double),
                 ("newton_terms", ctypes.c_int), ("lanes_per_system", ctypes.c_int),
                 ("block_size", ctypes.c_int), ("steps_per_launch", ctypes.c_longlong),
-                ("close_encounter_hill", ctypes.c_double), ("eject_factor", ctypes.c_double)]
+                ("close_encounter_hill", ctypes.c_double), ("eject_factor", ctypes.c_double),
+                ("graph_launches", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -275,7 +276,7 @@ class Integrator:
     def __init__(self, n_systems: int, max_planets: int, gr_mode: int = 1, c_light: float | None = None,
                  newton_terms: int = 8, lanes_per_system: int = 0, block_size: int = 0,
                  steps_per_launch: int = 0, close_encounter_hill: float = 0.0,
-                 eject_factor: float = 0.0, stream=None):
+                 eject_factor: float = 0.0, graph_launches: int = 0, stream=None):
         opt = whg_default_options()
         opt.gr_mode = gr_mode
         if c_light is not None:
@@ -286,6 +287,7 @@ class Integrator:
         opt.steps_per_launch = steps_per_launch
         opt.close_encounter_hill = close_encounter_hill
         opt.eject_factor = eject_factor
+        opt.graph_launches = graph_launches
         self.S, self.N = int(n_systems), int(max_planets)
         self.stream = stream if stream is not None else current_stream()
         self.ctx = whg_create(self.S, self.N, opt, self.stream)
