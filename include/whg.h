@@ -241,6 +241,16 @@ int whg_integrate_noalloc(int n_systems, int max_planets, const whg_options* opt
  * flops).  Blocks. */
 int whg_measure_fp64_tflops(double seconds, double* tflops);
 
+/* Solver search of Appendix A: n massless particles (DEVICE q, v [n][3]) each
+ * drifted `steps` times by time h around a central mass mu with its own
+ * solver configuration cfg [n][4] = (Halley iterations, Halley series terms,
+ * Newton iterations, Newton series terms), terms 1..12; G_n after the last
+ * iteration evaluated at the final X with the Newton series length.  Plain
+ * per-particle loops (a validation tool, not the integration path).
+ * Writes q_out, v_out (DEVICE).  Blocks. */
+int whg_kepler_sweep(const double* q, const double* v, const int* cfg, int n, double mu, double h,
+                     long long steps, double* q_out, double* v_out);
+
 /* The library's own reciprocal and reciprocal square root next to CUDA's, for
  * testing: out [4][n] DEVICE buffer receives rcp_own(x), 1/x (CUDA, IEEE),
  * rsqrt_own(x), rsqrt(x) (CUDA) for the n DEVICE inputs x (x > 0 for the

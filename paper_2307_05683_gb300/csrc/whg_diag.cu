@@ -25,6 +25,71 @@ __global__ void __launch_bounds__(256) k_dfma_loop(double* out, int iters, doubl
     out[tid] = s;
 }
 
+// Kepler drift with runtime iteration counts and series lengths, for the
+// solver search of Appendix A: 1/k! for k = 0..31 in constant memory; the
+// G_n after the last iteration are evaluated at the final X with the Newton
+// series length (the definition the oracle uses).
+__constant__ double c_invfact[32];
+
+__device__ __forceinline__ void stumpff_rt(double z, int T, double& c2, double& c3)
+{
+    c2 = c_invfact[2 * T];
+    c3 = c_invfact[2 * T + 1];
+    for (int k = T - 2; k >= 0; --k) {
+        c2 = fma(-z, c2, c_invfact[2 * k + 2]);
+        c3 = fma(-z, c3, c_invfact[2 * k + 3]);
+    }
+}
+
+__global__ void k_kepler_sweep(const double* q, const double* v, const int* cfg, int n, double mu, double h,
+                               long long steps, double* qo, double* vo)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double qx = q[3 * i], qy = q[3 * i + 1], qz = q[3 * i + 2];
+    double vx = v[3 * i], vy = v[3 * i + 1], vz = v[3 * i + 2];
+    // clamped: series of 1..12 terms keep every table index below 32
+    const int hi = min(max(cfg[4 * i], 0), 16), ht = min(max(cfg[4 * i + 1], 1), 12);
+    const int ni = min(max(cfg[4 * i + 2], 0), 16), nt = min(max(cfg[4 * i + 3], 1), 12);
+    for (long long s = 0; s < steps; ++s) {
+        const double r0 = sqrt(qx * qx + qy * qy + qz * qz);
+        const double eta0 = qx * vx + qy * vy + qz * vz;
+        const double beta = 2.0 * mu / r0 - (vx * vx + vy * vy + vz * vz);
+        const double zeta0 = mu - beta * r0;
+        double X = h / r0 - eta0 * h * h / (2.0 * r0 * r0 * r0);
+        double c2, c3;
+        for (int it = 0; it < hi + ni; ++it) {
+            const int T = it < hi ? ht : nt;
+            const double X2 = X * X;
+            stumpff_rt(beta * X2, T, c2, c3);
+            const double G2 = X2 * c2, G3 = X2 * X * c3;
+            const double G0 = 1.0 - beta * G2, G1 = X - beta * G3;
+            const double F = r0 * G1 + eta0 * G2 + mu * G3 - h;
+            const double Fp = r0 * G0 + eta0 * G1 + mu * G2;
+            if (it < hi) {
+                const double Fpp = eta0 * G0 + zeta0 * G1;
+                X = X - 2.0 * F * Fp / (2.0 * Fp * Fp - F * Fpp);
+            } else {
+                X = X - F / Fp;
+            }
+        }
+        const double X2 = X * X;
+        stumpff_rt(beta * X2, nt, c2, c3);
+        const double G2 = X2 * c2, G3 = X2 * X * c3;
+        const double G0 = 1.0 - beta * G2, G1 = X - beta * G3;
+        const double r = r0 * G0 + eta0 * G1 + mu * G2;
+        const double f = 1.0 - mu * G2 / r0, g = h - mu * G3;
+        const double fd = -mu * G1 / (r * r0), gd = 1.0 - mu * G2 / r;
+        const double nqx = f * qx + g * vx, nqy = f * qy + g * vy, nqz = f * qz + g * vz;
+        vx = fd * qx + gd * vx;
+        vy = fd * qy + gd * vy;
+        vz = fd * qz + gd * vz;
+        qx = nqx; qy = nqy; qz = nqz;
+    }
+    qo[3 * i] = qx; qo[3 * i + 1] = qy; qo[3 * i + 2] = qz;
+    vo[3 * i] = vx; vo[3 * i + 1] = vy; vo[3 * i + 2] = vz;
+}
+
 __global__ void k_special(const double* x, int n, double* out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -74,6 +139,29 @@ int whg_measure_fp64_tflops(double seconds, double* tflops)
     cudaEventDestroy(e1);
     cudaFree(out);
     return rc;
+}
+
+int whg_kepler_sweep(const double* q, const double* v, const int* cfg, int n, double mu, double h,
+                     long long steps, double* q_out, double* v_out)
+{
+    if (!q || !v || !cfg || !q_out || !v_out || n < 0 || steps < 0 || !(mu > 0.0) || !(h > 0.0))
+        return WHG_EINVAL;
+    if (n == 0) return WHG_OK;
+    static bool table_ready = false;      // 1/k!, k = 0..31, rounded once from the exact factorial
+    if (!table_ready) {
+        double t[32];
+        long double f = 1.0L;
+        for (int k = 0; k < 32; ++k) {
+            if (k > 1) f *= (long double)k;
+            t[k] = (double)(1.0L / f);
+        }
+        if (cudaMemcpyToSymbol(c_invfact, t, sizeof t) != cudaSuccess) return WHG_ECUDA;
+        table_ready = true;
+    }
+    k_kepler_sweep<<<(n + 127) / 128, 128>>>(q, v, cfg, n, mu, h, steps, q_out, v_out);
+    if (cudaGetLastError() != cudaSuccess) return WHG_ECUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return WHG_ECUDA;
+    return WHG_OK;
 }
 
 int whg_test_special(const double* x, int n, double* out)

@@ -76,6 +76,8 @@ def load():
             "whg_destroy": (None, [P]),
             "whg_measure_fp64_tflops": (ctypes.c_int, [ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
             "whg_test_special": (ctypes.c_int, [D, ctypes.c_int, D]),
+            "whg_kepler_sweep": (ctypes.c_int, [D, D, I, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                ctypes.c_longlong, D, D]),
             "whg_adjoint_forward": (ctypes.c_int, [P, ctypes.c_longlong, ctypes.c_int, D, D]),
             "whg_adjoint_backward": (ctypes.c_int, [P, D, D, D, D]),
             "whg_integrate_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int,
@@ -97,7 +99,7 @@ def exported_symbols() -> list[str]:
             "whg_energy_device", "whg_get_raw", "whg_set_raw", "whg_synchronize",
             "whg_launch_count", "whg_last_error", "whg_destroy", "whg_measure_fp64_tflops",
             "whg_test_special", "whg_integrate_noalloc", "whg_adjoint_forward",
-            "whg_adjoint_backward"]
+            "whg_adjoint_backward", "whg_kepler_sweep"]
 
 
 def _check(ctx, rc: int) -> None:
@@ -244,6 +246,13 @@ def whg_measure_fp64_tflops(seconds: float = 0.5) -> float:
     out = ctypes.c_double()
     _check(None, load().whg_measure_fp64_tflops(float(seconds), ctypes.byref(out)))
     return out.value
+
+
+def whg_kepler_sweep(q, v, cfg, mu: float, h: float, steps: int, q_out, v_out) -> None:
+    _check(None, load().whg_kepler_sweep(_dev(q, "torch.float64"), _dev(v, "torch.float64"),
+                                         _dev(cfg, "torch.int32"), int(q.shape[0]), float(mu), float(h),
+                                         int(steps), _dev(q_out, "torch.float64"),
+                                         _dev(v_out, "torch.float64")))
 
 
 def whg_test_special(x, out) -> None:
