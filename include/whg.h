@@ -93,6 +93,10 @@ typedef struct {
                                  step launches (captured once per init and launch length)
                                  for the whole multiples, and launches the rest directly.
                                  Results are bitwise those of direct launches. */
+    int merge_jumps;          /* 1: without the GR term, one J(dt) followed by I(dt) per step
+                                 instead of J(dt/2) I(dt) J(dt/2): J and I commute when there
+                                 is no GR term (Sec. 3.1), so this is the same map up to
+                                 rounding, one jump cheaper.  Ignored when gr_mode != 0. */
 } whg_options;
 
 /* Fill *opt with the defaults above. */

@@ -75,7 +75,7 @@ def _load():
         lib.orc_create.restype = P
         lib.orc_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                   ctypes.c_double, ctypes.c_double]
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_int]
         lib.orc_destroy.argtypes = [P]
         lib.orc_init.argtypes = [P, D, D, D, I, D]
         lib.orc_init.restype = ctypes.c_int
@@ -115,13 +115,13 @@ class OracleEnsemble:
     def __init__(self, n_systems: int, max_planets: int, gr_mode: int = 0,
                  c_light: float = C_LIGHT_DEFAULT, newton_terms: int = 8,
                  halley_terms: int = 4, halley_iters: int = 2, newton_iters: int = 2,
-                 encounter_hill: float = 0.0, eject_factor: float = 0.0):
+                 encounter_hill: float = 0.0, eject_factor: float = 0.0, merge_jumps: bool = False):
         self._lib = _load()
         self.S, self.N = int(n_systems), int(max_planets)
         self._h = self._lib.orc_create(self.S, self.N, int(gr_mode), float(c_light),
                                        int(halley_iters), int(halley_terms),
                                        int(newton_iters), int(newton_terms),
-                                       float(encounter_hill), float(eject_factor))
+                                       float(encounter_hill), float(eject_factor), int(merge_jumps))
         if not self._h:
             raise ValueError("orc_create: invalid arguments")
 
@@ -205,14 +205,14 @@ def _load_tangent():
             D = ctypes.POINTER(ctypes.c_double)
             lib.orc_tangent_loss.argtypes = [ctypes.c_int, D, D, D, ctypes.c_double, D, ctypes.c_longlong,
                                              ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
-                                             ctypes.c_int, ctypes.c_int, D, D]
+                                             ctypes.c_int, ctypes.c_int, ctypes.c_int, D, D]
             lib.orc_tangent_loss.restype = ctypes.c_int
             _tlib = lib
         return _tlib
 
 
 def tangent_gradient(masses, pos, vel, n_planets, dt, target, n_steps, gr_mode=1,
-                     c_light=C_LIGHT_DEFAULT, newton_terms=8):
+                     c_light=C_LIGHT_DEFAULT, newton_terms=8, merge_jumps=False):
     """Gradient of L = sum_i |Q_i(T) - target_i|^2 (synchronized heliocentric
     positions after n_steps) for ONE system, by forward-mode derivatives of the
     oracle's map, one input direction per pass.  Returns (L, dL/dpos [1+n][3],
@@ -232,14 +232,15 @@ def tangent_gradient(masses, pos, vel, n_planets, dt, target, n_steps, gr_mode=1
         for k in range(1 + n):
             for c in range(3):
                 rc = lib.orc_tangent_loss(n, _d(m), _d(x), _d(u), float(dt), _d(T), int(n_steps),
-                                          int(gr_mode), float(c_light), int(newton_terms), kind, k, c,
-                                          _d(L), _d(dL))
+                                          int(gr_mode), float(c_light), int(newton_terms),
+                                          int(merge_jumps), kind, k, c, _d(L), _d(dL))
                 if rc:
                     raise RuntimeError("orc_tangent_loss failed (frozen system?)")
                 out[k, c] = dL[0]
     for k in range(1 + n):
         rc = lib.orc_tangent_loss(n, _d(m), _d(x), _d(u), float(dt), _d(T), int(n_steps), int(gr_mode),
-                                  float(c_light), int(newton_terms), 2, k, 0, _d(L), _d(dL))
+                                  float(c_light), int(newton_terms), int(merge_jumps), 2, k, 0, _d(L),
+                                  _d(dL))
         if rc:
             raise RuntimeError("orc_tangent_loss failed (frozen system?)")
         gm[k] = dL[0]

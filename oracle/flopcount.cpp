@@ -52,7 +52,7 @@ int main(int argc, char** argv)
     orc_options opt;
     opt.gr_mode = gr; opt.c_light = 10065.32; opt.halley_iters = 2; opt.halley_terms = 4;
     opt.newton_iters = 2; opt.newton_terms = nt;
-    opt.encounter_hill = 0.0; opt.eject_factor = 0.0;
+    opt.encounter_hill = 0.0; opt.eject_factor = 0.0; opt.merge_jumps = 0;
     orc_system s = orc_system();
     s.n = n; s.m0 = 1.0; s.dt = 0.01; s.M = 1.0; s.nstep = 1;   /* steady state: K(dt) */
     for (int i = 0; i < n; ++i) {

@@ -29,7 +29,9 @@
  *     kicks v_i by h a_GR(Q_i) (canonical in these coordinates); gr_mode 2 also
  *     subtracts sum_j (m_j/m_0) a_GR(Q_j) from every planet (the literal
  *     reading of the back-reaction sentence).
- *   - the two J(dt/2) half-steps are always applied separately.
+ *   - the two J(dt/2) half-steps are applied separately, unless merge_jumps
+ *     is set and the GR term is off: then one J(dt) precedes I(dt), the
+ *     combination Sec. 3.1 allows because J and I commute without GR.
  *   - the interaction visits each unordered pair once (Newton's third law,
  *     Sec. 3.3), in plain i < j order.
  *   - a system whose step produces a non-finite value, or that starts a
@@ -83,6 +85,7 @@ typedef struct {
     int newton_terms;    /* 8 (Sec. 3.2) or 6 (Appendix A) */
     double encounter_hill; /* stop rule: pair closer than this many mutual Hill radii (0 = off) */
     double eject_factor;   /* stop rule: |Q_i| beyond this many initial outermost a (0 = off) */
+    int merge_jumps;       /* without GR: one J(dt) then I(dt) instead of J(dt/2) I(dt) J(dt/2) */
 } orc_options;
 
 /* One system in democratic heliocentric coordinates (Sec. 3.1).
@@ -317,10 +320,16 @@ static void orc_step(orc_system* s, long long n, const orc_options* opt)
                 if (!(beta > 0.0)) bad |= ORC_STATUS_HYPERBOLIC;
             }
         }
-        orc_jump(s, 0.5 * s->dt);
-        if (orc_interaction(s, s->dt, opt)) bad |= ORC_STATUS_CLOSE_ENCOUNTER;
-        if (opt->gr_mode) orc_gr_kick(s, s->dt, opt);
-        orc_jump(s, 0.5 * s->dt);
+        if (opt->merge_jumps && !opt->gr_mode) {
+            /* J commutes with I when there is no GR term (Sec. 3.1): J(dt) I(dt) */
+            orc_jump(s, s->dt);
+            if (orc_interaction(s, s->dt, opt)) bad |= ORC_STATUS_CLOSE_ENCOUNTER;
+        } else {
+            orc_jump(s, 0.5 * s->dt);
+            if (orc_interaction(s, s->dt, opt)) bad |= ORC_STATUS_CLOSE_ENCOUNTER;
+            if (opt->gr_mode) orc_gr_kick(s, s->dt, opt);
+            orc_jump(s, 0.5 * s->dt);
+        }
         if (!orc_state_finite(s)) bad |= ORC_STATUS_NONFINITE;
         if (bad) {
             memcpy(s->Q, Qs, sizeof(Qs));

@@ -26,7 +26,7 @@ typedef struct {
 
 orc_ensemble* orc_create(int S, int Nmax, int gr_mode, double c_light, int halley_iters,
                          int halley_terms, int newton_iters, int newton_terms,
-                         double encounter_hill, double eject_factor)
+                         double encounter_hill, double eject_factor, int merge_jumps)
 {
     orc_ensemble* e;
     if (S < 1 || Nmax < 1 || Nmax > ORC_NMAX) return NULL;
@@ -46,6 +46,7 @@ orc_ensemble* orc_create(int S, int Nmax, int gr_mode, double c_light, int halle
     e->opt.newton_terms = newton_terms;
     e->opt.encounter_hill = encounter_hill;
     e->opt.eject_factor = eject_factor;
+    e->opt.merge_jumps = merge_jumps;
     return e;
 }
 

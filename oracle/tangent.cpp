@@ -44,8 +44,8 @@ static double orc_mass_value(Dual x) { return x.v; }
 
 extern "C" int orc_tangent_loss(int n, const double* m, const double* x, const double* u, double dt,
                                 const double* target, long long nsteps, int gr_mode, double c_light,
-                                int newton_terms, int kind, int body, int comp, double* loss,
-                                double* dloss)
+                                int newton_terms, int merge_jumps, int kind, int body, int comp,
+                                double* loss, double* dloss)
 {
     if (n < 1 || n > ORC_NMAX || nsteps < 0) return -1;
     orc_options opt;
@@ -57,6 +57,7 @@ extern "C" int orc_tangent_loss(int n, const double* m, const double* x, const d
     opt.newton_terms = newton_terms;
     opt.encounter_hill = 0.0;
     opt.eject_factor = 0.0;
+    opt.merge_jumps = merge_jumps;
     Dual md[ORC_NMAX + 1], xd[3 * (ORC_NMAX + 1)], ud[3 * (ORC_NMAX + 1)];
     for (int k = 0; k <= n; ++k) {
         md[k] = Dual(m[k], (kind == 2 && body == k) ? 1.0 : 0.0);

@@ -314,11 +314,12 @@ __device__ __forceinline__ void tape_body(const WhgState& st, const WhgBuckets& 
         kepler_drift<NT>(mu, h, qx, qy, qz, vx, vy, vz, X);
         tp[6 * NL] = X;
         tp[7 * NL] = vx; tp[8 * NL] = vy; tp[9 * NL] = vz;
-        jump<L>(g, m, c, vx, vy, vz, qx, qy, qz);
+        const bool merged = GRM == 0 && st.merge;
+        jump<L>(g, m, merged ? 2.0 * c : c, vx, vy, vz, qx, qy, qz);
         tp[10 * NL] = qx; tp[11 * NL] = qy; tp[12 * NL] = qz;
         kick<L, GRM>(g, qx, qy, qz, hm, mrat, kgr, nothr, vx, vy, vz);
         tp[13 * NL] = vx; tp[14 * NL] = vy; tp[15 * NL] = vz;
-        jump<L>(g, m, c, vx, vy, vz, qx, qy, qz);
+        if (!merged) jump<L>(g, m, c, vx, vy, vz, qx, qy, qz);
         if (!real) {                                  // lanes without a planet stay parked
             qx = pqx; qy = pqy; qz = pqz;
             vx = pvx; vy = pvy; vz = pvz;
@@ -357,9 +358,10 @@ __device__ __forceinline__ void back_body(const WhgState& st, const WhgBuckets& 
         const double q2x = tp[10 * NL], q2y = tp[11 * NL], q2z = tp[12 * NL];
         const double v3x = tp[13 * NL], v3y = tp[14 * NL], v3z = tp[15 * NL];
         const double h = (s0 + k == 0) ? 0.5 * dt : dt;
-        jump_vjp<L>(g, m, c, mu, v3x, v3y, v3z, lqx, lqy, lqz, lvx, lvy, lvz, lm, lmu);
+        const bool merged = GRM == 0 && st.merge;
+        if (!merged) jump_vjp<L>(g, m, c, mu, v3x, v3y, v3z, lqx, lqy, lqz, lvx, lvy, lvz, lm, lmu);
         kick_vjp<L, GRM>(g, q2x, q2y, q2z, m, hm, dt, mu, kgr, lvx, lvy, lvz, lqx, lqy, lqz, lm, lmu);
-        jump_vjp<L>(g, m, c, mu, v1x, v1y, v1z, lqx, lqy, lqz, lvx, lvy, lvz, lm, lmu);
+        jump_vjp<L>(g, m, merged ? 2.0 * c : c, mu, v1x, v1y, v1z, lqx, lqy, lqz, lvx, lvy, lvz, lm, lmu);
         kepler_vjp<NT>(mu, h, q0x, q0y, q0z, v0x, v0y, v0z, X, lqx, lqy, lqz, lvx, lvy, lvz, lmu);
         if (!real) {
             lqx = lqy = lqz = lvx = lvy = lvz = lm = lmu = 0.0;

@@ -546,9 +546,15 @@ __device__ __forceinline__ void step_body(const WhgState& st, const WhgBuckets& 
         const double r0sq = fma(qx, qx, fma(qy, qy, qz * qz));
         const bool far = __double_as_longlong(r0sq) > __double_as_longlong(rej2);
         const bool bound = kepler_drift<NT>(mu, hK, qx, qy, qz, vx, vy, vz);
-        jump<L>(g, m, jc, vx, vy, vz, qx, qy, qz);
-        const bool close = kick<L, GRM>(g, qx, qy, qz, hm, mrat, kgr, thr2, vx, vy, vz);
-        jump<L>(g, m, jc, vx, vy, vz, qx, qy, qz);
+        bool close;
+        if (GRM == 0 && st.merge) {                   // J(dt) I(dt): J and I commute without GR
+            jump<L>(g, m, 2.0 * jc, vx, vy, vz, qx, qy, qz);
+            close = kick<L, GRM>(g, qx, qy, qz, hm, mrat, kgr, thr2, vx, vy, vz);
+        } else {
+            jump<L>(g, m, jc, vx, vy, vz, qx, qy, qz);
+            close = kick<L, GRM>(g, qx, qy, qz, hm, mrat, kgr, thr2, vx, vy, vz);
+            jump<L>(g, m, jc, vx, vy, vz, qx, qy, qz);
+        }
         const bool fin = is_finite(qx) & is_finite(qy) & is_finite(qz) & is_finite(vx) &
                          is_finite(vy) & is_finite(vz);
         const unsigned bad_h = __ballot_sync(WHG_FULL_MASK, real && !bound) & gmask;

@@ -33,6 +33,7 @@ struct WhgState {
     double c_light;
     double hill;                     // close-encounter rule: mutual Hill radii (0 = off)
     double eject;                    // ejection rule: factor on the largest initial a (0 = off)
+    int merge;                       // one J(dt) before I(dt) (GR off only)
 };
 
 // Bucket table (by value in every launch).

@@ -130,6 +130,7 @@ extern "C" int whg_integrate_noalloc(int n_systems, int max_planets, const whg_o
     st.c_light = opt.c_light;
     st.hill = opt.close_encounter_hill;
     st.eject = opt.eject_factor;
+    st.merge = (opt.merge_jumps && opt.gr_mode == 0) ? 1 : 0;
 
     WhgBuckets bk{};
     bk.nb = 1;

@@ -37,7 +37,7 @@ class whg_options(ctypes.Structure):
                 ("newton_terms", ctypes.c_int), ("lanes_per_system", ctypes.c_int),
                 ("block_size", ctypes.c_int), ("steps_per_launch", ctypes.c_longlong),
                 ("close_encounter_hill", ctypes.c_double), ("eject_factor", ctypes.c_double),
-                ("graph_launches", ctypes.c_int)]
+                ("graph_launches", ctypes.c_int), ("merge_jumps", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -285,7 +285,8 @@ class Integrator:
     def __init__(self, n_systems: int, max_planets: int, gr_mode: int = 1, c_light: float | None = None,
                  newton_terms: int = 8, lanes_per_system: int = 0, block_size: int = 0,
                  steps_per_launch: int = 0, close_encounter_hill: float = 0.0,
-                 eject_factor: float = 0.0, graph_launches: int = 0, stream=None):
+                 eject_factor: float = 0.0, graph_launches: int = 0, merge_jumps: bool = False,
+                 stream=None):
         opt = whg_default_options()
         opt.gr_mode = gr_mode
         if c_light is not None:
@@ -297,6 +298,7 @@ class Integrator:
         opt.close_encounter_hill = close_encounter_hill
         opt.eject_factor = eject_factor
         opt.graph_launches = graph_launches
+        opt.merge_jumps = int(merge_jumps)
         self.S, self.N = int(n_systems), int(max_planets)
         self.stream = stream if stream is not None else current_stream()
         self.ctx = whg_create(self.S, self.N, opt, self.stream)

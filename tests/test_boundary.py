@@ -58,5 +58,5 @@ def test_options_struct_layout(lib_path):
     assert o.gr_mode == 1 and o.newton_terms == 8
     assert o.c_light == pytest.approx(10065.32, rel=1e-5)
     assert o.close_encounter_hill == 0.0 and o.eject_factor == 0.0
-    assert o.graph_launches == 0
+    assert o.graph_launches == 0 and o.merge_jumps == 0
     assert ctypes.sizeof(whg.whg_options) == 64

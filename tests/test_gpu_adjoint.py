@@ -26,10 +26,10 @@ def _t(a, dtype=None):
     return torch.tensor(a, dtype=dtype or torch.float64, device="cuda")
 
 
-def gpu_grad(whg, ens, target, n, K, gr_mode=1, lanes=0):
+def gpu_grad(whg, ens, target, n, K, gr_mode=1, lanes=0, **kw):
     import torch
     S, N = ens.n_systems, ens.max_planets
-    it = whg.Integrator(S, N, gr_mode=gr_mode, lanes_per_system=lanes)
+    it = whg.Integrator(S, N, gr_mode=gr_mode, lanes_per_system=lanes, **kw)
     whg.whg_init_device(it.ctx, _t(ens.masses), _t(ens.pos), _t(ens.vel), _t(ens.n_planets, torch.int32),
                         _t(ens.dt))
     loss = torch.empty(S, dtype=torch.float64, device="cuda")
@@ -61,8 +61,8 @@ def _targets(ens, seed, spread=0.05):
     return T * live[..., None]
 
 
-@pytest.mark.parametrize("gr_mode", [0, 1, 2])
-def test_adjoint_matches_oracle_tangent(whg, orc, gr_mode):
+@pytest.mark.parametrize("gr_mode,merge", [(0, False), (1, False), (2, False), (0, True)])
+def test_adjoint_matches_oracle_tangent(whg, orc, gr_mode, merge):
     """Every input direction of a few systems (8-planet and compact mixed),
     1000 steps, checkpoints every 100: the adjoint equals the oracle's
     forward-mode derivative to 1e-8 of the largest gradient entry."""
@@ -73,11 +73,11 @@ def test_adjoint_matches_oracle_tangent(whg, orc, gr_mode):
                            np.concatenate([ens.n_planets, cmp.n_planets]), np.concatenate([ens.dt, cmp.dt]))
     T = _targets(both, 1)
     n = 1000
-    loss, gx, gu, gm = gpu_grad(whg, both, T, n, 100, gr_mode=gr_mode)
+    loss, gx, gu, gm = gpu_grad(whg, both, T, n, 100, gr_mode=gr_mode, merge_jumps=merge)
     for s in range(both.n_systems):
         k = int(both.n_planets[s])
         L, tx, tu, tm = orc.tangent_gradient(both.masses[s], both.pos[s], both.vel[s], k, both.dt[s], T[s],
-                                             n, gr_mode=gr_mode)
+                                             n, gr_mode=gr_mode, merge_jumps=merge)
         assert loss[s] == pytest.approx(L, rel=1e-11)
         for a, b in ((gx[s, :1 + k], tx), (gu[s, :1 + k], tu)):
             assert np.abs(a - b).max() <= 1e-8 * np.abs(b).max()

@@ -36,8 +36,8 @@ def gpu_run(whg, ens, n, chunks=None, **kw):
     return out
 
 
-def oracle_run(orc, ens, n, gr_mode=1, newton_terms=8, c_light=None):
-    kw = dict(gr_mode=gr_mode, newton_terms=newton_terms)
+def oracle_run(orc, ens, n, gr_mode=1, newton_terms=8, c_light=None, **extra):
+    kw = dict(gr_mode=gr_mode, newton_terms=newton_terms, **extra)
     if c_light is not None:
         kw["c_light"] = c_light
     o = orc.OracleEnsemble(ens.n_systems, ens.max_planets, **kw)
@@ -421,3 +421,15 @@ def test_device_init_mixed_planet_counts(whg, orc):
     out = b.read_state()
     for u, v in zip(ref, out):
         assert np.array_equal(u, v)
+
+
+@pytest.mark.parametrize("n,tol", [(1, 1e-12), (10000, 1e-9)])
+def test_merged_jumps_match_oracle(whg, orc, n, tol):
+    """Without GR, one J(dt) before I(dt) per step (Sec. 3.1), on both sides."""
+    ens = inputs.two_planet_system(0, 10)
+    g = gpu_run(whg, ens, n, gr_mode=0, merge_jumps=True)
+    o = oracle_run(orc, ens, n, gr_mode=0, merge_jumps=True)
+    assert_parity(g, o, tol, ens.n_planets)
+    s = inputs.solar_ensemble(13, 64)
+    assert_parity(gpu_run(whg, s, 500, gr_mode=0, merge_jumps=True),
+                  oracle_run(orc, s, 500, gr_mode=0, merge_jumps=True), 1e-11, s.n_planets)

@@ -338,3 +338,24 @@ def test_nonfinite_step_rolls_back_and_freezes(orc):
     assert t[0] == pytest.approx(10 * ens.dt[0]) and t[1] == 0.0
     assert np.array_equal(pos[1], o.read_state()[0][1])
     assert np.all(np.isfinite(pos[1]))
+
+
+def test_merged_jumps_are_the_same_map_without_gr(orc):
+    """Sec. 3.1: without GR the jump commutes with the interaction, so
+    J(dt/2) I(dt) J(dt/2) and J(dt) I(dt) are the same map (rounding aside);
+    with the GR term the option is ignored."""
+    ens = inputs.solar_ensemble(12, 3)
+    a = make(orc, ens, gr_mode=0)
+    b = make(orc, ens, gr_mode=0, merge_jumps=True)
+    a.step(500)
+    b.step(500)
+    pa, va, _, _ = a.read_state()
+    pb, vb, _, _ = b.read_state()
+    assert np.abs(pa - pb).max() < 1e-12 * np.abs(pa).max()
+    assert not np.array_equal(pa, pb)                    # a different operation order
+    c = make(orc, ens, gr_mode=1)
+    d = make(orc, ens, gr_mode=1, merge_jumps=True)
+    c.step(100)
+    d.step(100)
+    for x, y in zip(c.get_raw(), d.get_raw()):
+        assert np.array_equal(x, y)
