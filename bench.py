@@ -45,6 +45,15 @@ UNIT = "system-steps/s"
 # operation); key (planets, newton_terms, gr_mode).  A CPU test keeps this
 # table equal to the oracle's count.
 ALG_FLOPS = {(8, 8, 1): 3360, (8, 8, 0): 3232, (8, 6, 1): 3168, (8, 8, 2): 3432}
+# Of these, the Kepler solver's starting phase (initial guess and the two
+# Halley steps, 8 drifts): with the halley_fp32 option they run on the FP32
+# pipe, and that option's FP64 roofline counts ALG_FLOPS - START_FLOPS.
+START_FLOPS = {(8, 8, 1): 768, (8, 8, 0): 768, (8, 6, 1): 768, (8, 8, 2): 768}
+
+
+def fp64_flops(gr_mode: int, halley_fp32: bool, newton_terms: int = 8) -> int:
+    key = (8, newton_terms, gr_mode)
+    return ALG_FLOPS[key] - (START_FLOPS[key] if halley_fp32 else 0)
 
 # FP64 peak from the unit counts and clocks: 152 SMs x 2 FP64 FMA lanes per
 # clock (1.25 TFLOP/s nominal / (152 x 2.07 GHz x 2)) x 2 flops x 2.07 GHz.
@@ -63,6 +72,9 @@ def parse_args():
     p.add_argument("--systems", type=int, default=4096)
     p.add_argument("--chunk", type=int, default=10000, help="integrator steps per benchmark step")
     p.add_argument("--gr-mode", type=int, default=1)
+    p.add_argument("--halley-fp32", type=int, choices=[0, 1], default=0,
+                   help="Kepler solver's initial guess and Halley steps in FP32 (1, an option) "
+                        "or FP64 (0, the library default: every step in FP64)")
     p.add_argument("--block-size", type=int, default=0)
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU work of the oracle sample")
@@ -77,6 +89,10 @@ def workload(args) -> dict:
             "systems_per_gpu": args.systems, "planets": 8,
             "integrator_steps_per_bench_step": args.chunk,
             "gr_mode": args.gr_mode, "newton_terms": 8, "halley_terms": 4,
+            "kepler_solver": ("initial guess + 2 Halley steps (4-term series) in FP32, 2 Newton steps "
+                              "(8-term series) and f, g in FP64" if args.halley_fp32 else
+                              "initial guess, 2 Halley steps (4-term series), 2 Newton steps (8-term series) "
+                              "and f, g all in FP64"),
             "l2": "state register-resident during a launch; 256 MB L2 flush between timed steps"}
 
 
@@ -260,16 +276,13 @@ def measure_adjoint(whg, torch, systems=1024, steps=10000, every=100, seed=4242)
     return res
 
 
-def throughput_sweep(whg, torch, sizes=tuple(1 << k for k in range(14, 21)), window_s=0.4, seed=77):
-    """System-steps/s and FP64 fraction against ensemble size (Solar-System-
-    shaped systems, GR on, default launch configuration), each point timed
-    with CUDA events over a window of about window_s after a warm-up call."""
-    base = inputs.solar_ensemble(seed, 4096)
-    out = []
-    stream = torch.cuda.Stream()
-    for S in sizes:
-        ens = base.tile(S)
-        it = whg.Integrator(S, 8, gr_mode=1, stream=stream.cuda_stream)
+def time_rate(whg, torch, ens, window_s: float, stream, **kw) -> tuple[float, int]:
+    """System-steps/s of one Integrator configuration on `ens`, CUDA events
+    on the library's stream over a window of about window_s after a warm-up
+    call of the same length."""
+    S = ens.n_systems
+    it = whg.Integrator(S, ens.max_planets, stream=stream.cuda_stream, **kw)
+    try:
         it.init(ens)
         n = max(32, int(2.4e8 * window_s / S))
         it.step(n)
@@ -279,10 +292,37 @@ def throughput_sweep(whg, torch, sizes=tuple(1 << k for k in range(14, 21)), win
         it.step(n)
         e1.record(stream)
         e1.synchronize()
-        rate = S * n / (e0.elapsed_time(e1) / 1e3)
+        return S * n / (e0.elapsed_time(e1) / 1e3), n
+    finally:
         it.close()
+
+
+def throughput_sweep(whg, torch, sizes=tuple(1 << k for k in range(14, 21)), window_s=0.4, seed=77):
+    """System-steps/s and FP64 fraction against ensemble size (Solar-System-
+    shaped systems, GR on, default launch configuration and solver), each
+    point timed with CUDA events over a window of about window_s after a
+    warm-up call."""
+    base = inputs.solar_ensemble(seed, 4096)
+    out = []
+    stream = torch.cuda.Stream()
+    for S in sizes:
+        rate, n = time_rate(whg, torch, base.tile(S), window_s, stream, gr_mode=1)
         out.append({"systems": S, "steps": n, "system_steps_per_s": round(rate, 1),
-                    "frac": round(rate * ALG_FLOPS[(8, 8, 1)] / 1e12 / FP64_PEAK_TFLOPS, 4)})
+                    "frac": round(rate * fp64_flops(1, False) / 1e12 / FP64_PEAK_TFLOPS, 4)})
+    return out
+
+
+def solver_comparison(whg, torch, ens, gr_mode: int, window_s=1.0):
+    """The bench workload with the whole Kepler solver in FP64 (the paper's
+    arithmetic) beside the default FP32 starting phase, same timing method."""
+    stream = torch.cuda.Stream()
+    out = {}
+    for h32 in (False, True):
+        rate, n = time_rate(whg, torch, ens, window_s, stream, gr_mode=gr_mode, halley_fp32=h32)
+        fl = fp64_flops(gr_mode, h32)
+        out["fp32_start" if h32 else "all_fp64"] = {
+            "system_steps_per_s": round(rate, 1), "steps": n, "fp64_flops_per_system_step": fl,
+            "frac": round(rate * fl / 1e12 / FP64_PEAK_TFLOPS, 4)}
     return out
 
 
@@ -303,7 +343,7 @@ def run_whg(args):
     ens = rank_workload(args, rank)
     stream = torch.cuda.Stream()
     it = whg.Integrator(S, 8, gr_mode=args.gr_mode, block_size=args.block_size,
-                        stream=stream.cuda_stream)
+                        halley_fp32=bool(args.halley_fp32), stream=stream.cuda_stream)
     it.init(ens)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     with torch.cuda.stream(stream):
@@ -375,17 +415,19 @@ def run_whg(args):
             dist.destroy_process_group()
         return
 
-    flops = ALG_FLOPS[(8, 8, args.gr_mode)]
+    flops = fp64_flops(args.gr_mode, bool(args.halley_fp32))
     kernel_ms = total_ms / args.steps / max(launches_per_step, 1.0)
     achieved = flops * S * (chunk / max(launches_per_step, 1.0)) / (kernel_ms / 1e3) / 1e12
     dfma = whg.whg_measure_fp64_tflops(0.5)
     adjoint = measure_adjoint(whg, torch) if world == 1 else None
     sweep = throughput_sweep(whg, torch) if world == 1 else None
+    solvers = solver_comparison(whg, torch, ens, args.gr_mode) if world == 1 else None
     roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                 "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
                 "traffic": profiled_traffic(),
                 "kernel": "k_step<8,8,1> (FP64 pipe)",
                 "algorithmic_flops_per_system_step": flops,
+                "fp32_flops_per_system_step": START_FLOPS[(8, 8, args.gr_mode)] if args.halley_fp32 else 0,
                 "peak_basis": "recipe unit counts x clocks: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz",
                 "dfma_loop_measured_tflops": round(dfma, 4),
                 "frac_of_measured_dfma_loop": round(achieved / dfma, 4)}
@@ -401,6 +443,7 @@ def run_whg(args):
             "gpu_launches": int(launches),
             "adjoint": adjoint,
             "sweep": sweep,
+            "solver_comparison": solvers,
             "clocks": clock_info,
             "systems_flagged": bad}
     it.close()
@@ -447,6 +490,7 @@ def run_reference(args):
             "ms_per_step": round(1e3 * wall / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded Solar-System-shaped ensemble)", "config": workload(args),
+            "note": "the oracle runs the whole Kepler solver in FP64",
             "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,

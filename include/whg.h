@@ -97,6 +97,16 @@ typedef struct {
                                  instead of J(dt/2) I(dt) J(dt/2): J and I commute when there
                                  is no GR term (Sec. 3.1), so this is the same map up to
                                  rounding, one jump cheaper.  Ignored when gr_mode != 0. */
+    int halley_fp32;          /* 1: the Kepler solver's initial guess and its 2 Halley steps
+                                 (Sec. 3.2) run in FP32; the 2 Newton steps, the f and g
+                                 functions and everything else stay FP64.  The Halley phase
+                                 only supplies the Newton phase's start, and two FP64 Newton
+                                 steps from a start within ~1e-7 converge quadratically to
+                                 FP64 rounding, so inside the solver's domain (Fig. 1) the
+                                 results match the all-FP64 solver to rounding.  Outside it
+                                 (pericentre timescale below ~2 steps) both are inaccurate and
+                                 may stop differently.  Default 0: the whole solver in FP64
+                                 (the paper's arithmetic). */
 } whg_options;
 
 /* Fill *opt with the defaults above. */
@@ -255,10 +265,22 @@ int whg_measure_fp64_tflops(double seconds, double* tflops);
 int whg_kepler_sweep(const double* q, const double* v, const int* cfg, int n, double mu, double h,
                      long long steps, double* q_out, double* v_out);
 
-/* The library's own reciprocal and reciprocal square root next to CUDA's, for
- * testing: out [4][n] DEVICE buffer receives rcp_own(x), 1/x (CUDA, IEEE),
- * rsqrt_own(x), rsqrt(x) (CUDA) for the n DEVICE inputs x (x > 0 for the
- * square roots).  Blocks. */
+/* FP64 pipe probe (no counterpart in the paper; it backs the lane layout):
+ * times, with CUDA events on the legacy default stream, one launch of
+ * warps_per_sm x (SM count) one-warp blocks running iters x 8 independent
+ * dependent-DFMA chains in the first active_lanes lanes of each warp (the
+ * others skip the loop).  *ms receives the kernel time.  warps_per_sm 1..64,
+ * active_lanes 1..32, iters 1..2^24; allocates and frees a small buffer;
+ * blocks.  On GB300 the time does not depend on active_lanes, so masked
+ * lanes cost full FP64 pipe time. */
+int whg_probe_fp64_lanes(int warps_per_sm, int active_lanes, int iters, float* ms);
+
+/* The library's own reciprocal, reciprocal square root and FP64 <-> FP32
+ * conversions next to CUDA's, for testing: out [6][n] DEVICE buffer receives
+ * rcp_own(x), 1/x (CUDA, IEEE), rsqrt_own(x), rsqrt(x) (CUDA) (x > 0 for the
+ * square roots, else 0), the own FP64 -> FP32 -> FP64 round trip of x, and
+ * CUDA's round-toward-zero FP64 -> FP32 conversion of x widened to FP64, for
+ * the n DEVICE inputs x.  Blocks. */
 int whg_test_special(const double* x, int n, double* out);
 
 #ifdef __cplusplus

@@ -247,10 +247,12 @@ def tangent_gradient(masses, pos, vel, n_planets, dt, target, n_steps, gr_mode=1
     return float(L[0]), gx, gu, gm
 
 
-def count_flops(n_planets: int, newton_terms: int = 8, gr_mode: int = 0) -> dict:
-    """Operations of one steady-state step of one system, counted on the oracle."""
+def count_flops(n_planets: int, newton_terms: int = 8, gr_mode: int = 0, halley_iters: int = 2) -> dict:
+    """Operations of one steady-state step of one system, counted on the oracle;
+    start_phase = those of the Kepler solver's initial guess and Halley steps."""
     _load()
-    out = subprocess.check_output([_FLOPS, str(n_planets), str(newton_terms), str(gr_mode)],
-                                  text=True).split()
-    adds, muls, divs, sqrts, flops = (int(v) for v in out)
-    return {"adds": adds, "muls": muls, "divs": divs, "sqrts": sqrts, "flops": flops}
+    out = subprocess.check_output([_FLOPS, str(n_planets), str(newton_terms), str(gr_mode),
+                                   str(halley_iters)], text=True).split()
+    adds, muls, divs, sqrts, flops, start = (int(v) for v in out)
+    return {"adds": adds, "muls": muls, "divs": divs, "sqrts": sqrts, "flops": flops,
+            "start_phase": start}

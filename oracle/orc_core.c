@@ -149,6 +149,12 @@ static void orc_stiefel(orc_real beta, orc_real X, int terms, orc_real G[4])
  * (Sec. 3.2, Eq. 3) for time h with mu = G m_0 (G = 1).  Universal variable X,
  * Kepler function F(X) = r_0 G_1 + eta_0 G_2 + mu G_3 - h, F' = r, F'' = dr/dX.
  * Fixed iteration count, no convergence test, no branches.  Writes beta. */
+/* Hook for the flop counter (flopcount.cpp): marks the solver's starting
+ * phase, the initial guess and the Halley steps.  No-op elsewhere. */
+#ifndef ORC_START_PHASE
+#define ORC_START_PHASE(on) ((void)0)
+#endif
+
 static void orc_kepler_drift(orc_mass mu, double h, orc_real Q[3], orc_real v[3],
                              const orc_options* opt, orc_real* beta_out)
 {
@@ -157,10 +163,11 @@ static void orc_kepler_drift(orc_mass mu, double h, orc_real Q[3], orc_real v[3]
     orc_real v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
     orc_real beta = 2.0 * mu / r0 - v2;
     orc_real zeta0 = mu - beta * r0;
-    orc_real X = h / r0 - eta0 * h * h / (2.0 * r0 * r0 * r0);
-    orc_real G[4];
+    orc_real X, G[4];
     int it;
     *beta_out = beta;
+    ORC_START_PHASE(1);
+    X = h / r0 - eta0 * h * h / (2.0 * r0 * r0 * r0);
 
     for (it = 0; it < opt->halley_iters; ++it) {           /* Halley's method */
         orc_stiefel(beta, X, opt->halley_terms, G);
@@ -171,6 +178,7 @@ static void orc_kepler_drift(orc_mass mu, double h, orc_real Q[3], orc_real v[3]
             X = X - 2.0 * F * Fp / (2.0 * Fp * Fp - F * Fpp);
         }
     }
+    ORC_START_PHASE(0);
     for (it = 0; it < opt->newton_iters; ++it) {           /* Newton's method */
         orc_stiefel(beta, X, opt->newton_terms, G);
         {

@@ -126,7 +126,8 @@ __device__ __forceinline__ void jump_vjp(const Group<L>& g, double m, double c, 
                                          double vy, double vz, double lqx, double lqy, double lqz,
                                          double& lvx, double& lvy, double& lvz, double& lm, double& lmu)
 {
-    const double Lx = group_sum<L>(g, lqx), Ly = group_sum<L>(g, lqy), Lz = group_sum<L>(g, lqz);
+    double Lx, Ly, Lz;
+    group_sum3<L>(g, lqx, lqy, lqz, Lx, Ly, Lz);
     lvx += c * m * Lx;
     lvy += c * m * Ly;
     lvz += c * m * Lz;
@@ -196,7 +197,8 @@ __device__ __forceinline__ void kick_vjp(const Group<L>& g, double qx, double qy
         const double c = kgr * (ri2 * ri2);
         double ax = lvx, ay = lvy, az = lvz;             // adjoint of this planet's a_GR
         if (GRM == 2) {
-            const double Lx = group_sum<L>(g, lvx), Ly = group_sum<L>(g, lvy), Lz = group_sum<L>(g, lvz);
+            double Lx, Ly, Lz;
+            group_sum3<L>(g, lvx, lvy, lvz, Lx, Ly, Lz);
             const double aL = c * (qx * Lx + qy * Ly + qz * Lz);   // a_i . Lambda_v
             lm -= aL / mu;
             lmu += m * aL / (mu * mu);
@@ -249,7 +251,7 @@ __device__ __forceinline__ void loss_body(const WhgState& st, const WhgBuckets& 
     const long long ns = pl.has_sys ? st.nstep[s] : 0;
     const bool real = pl.has_sys && g.p < st.nplan[s];
     double sx = qx, sy = qy, sz = qz, svx = vx, svy = vy, svz = vz, X = 0.0;
-    if (ns > 0) kepler_drift<NT>(mu, 0.5 * dt, sx, sy, sz, svx, svy, svz, X);
+    if (ns > 0) kepler_drift<NT>(mu, 0.5 * dt, sx, sy, sz, svx, svy, svz, X, st.halley32 != 0);
     const int u = pl.has_sys ? user_index(st, s) : 0;
     double ex = 0.0, ey = 0.0, ez = 0.0;
     if (real) {
@@ -311,7 +313,7 @@ __device__ __forceinline__ void tape_body(const WhgState& st, const WhgBuckets& 
         tp[3 * NL] = vx; tp[4 * NL] = vy; tp[5 * NL] = vz;
         const double h = (s0 + k == 0) ? 0.5 * dt : dt;
         double X;
-        kepler_drift<NT>(mu, h, qx, qy, qz, vx, vy, vz, X);
+        kepler_drift<NT>(mu, h, qx, qy, qz, vx, vy, vz, X, st.halley32 != 0);
         tp[6 * NL] = X;
         tp[7 * NL] = vx; tp[8 * NL] = vy; tp[9 * NL] = vz;
         const bool merged = GRM == 0 && st.merge;

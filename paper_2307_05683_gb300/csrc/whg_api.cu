@@ -200,6 +200,7 @@ void whg_default_options(whg_options* opt)
     opt->eject_factor = 0.0;
     opt->graph_launches = 0;
     opt->merge_jumps = 0;
+    opt->halley_fp32 = 0;
 }
 
 int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options* opt_in,
@@ -287,6 +288,7 @@ int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options*
     st.hill = opt.close_encounter_hill;
     st.eject = opt.eject_factor;
     st.merge = (opt.merge_jumps && opt.gr_mode == 0) ? 1 : 0;
+    st.halley32 = opt.halley_fp32 ? 1 : 0;
 
     const size_t B = 1 + (size_t)max_planets;
     const size_t sd = (size_t)n_systems * (7 * B + 1);

@@ -112,6 +112,40 @@ __device__ __forceinline__ double rsqrt_cubed(double x)
     return fma(y3 * e, fma(1.875, e, 1.5), y3);
 }
 
+// FP64 -> FP32 from the bit fields (sign, exponent rebiased from 1023 to
+// 127, mantissa truncated to 23 bits) on the integer pipe: the hardware
+// conversion runs on the FP64 pipe, the scarce unit here.  Rounds toward
+// zero; |x| below the FP32 normal range gives a signed zero, above it (and
+// inf, NaN) a signed infinity.
+__device__ __forceinline__ float to_f32(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    const unsigned sign = hi & 0x80000000u;
+    const int ex = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;            // FP32 biased exponent
+    unsigned b = sign | ((unsigned)ex << 23) | ((hi & 0x000fffffu) << 3) | (lo >> 29);
+    b = ex <= 0 ? sign : b;
+    b = ex >= 255 ? (sign | 0x7f800000u) : b;
+    return __uint_as_float(b);
+}
+
+// FP32 -> FP64 from the bit fields (exact for normal numbers; subnormals give
+// a signed zero; inf and NaN stay inf and NaN), on the integer pipe.
+__device__ __forceinline__ double to_f64(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned sign = b & 0x80000000u;
+    const unsigned ex = (b >> 23) & 0xffu;
+    const unsigned man = b & 0x007fffffu;
+    unsigned hi = sign | ((ex + 896u) << 20) | (man >> 3);
+    unsigned lo = man << 29;
+    hi = ex == 0u ? sign : hi;
+    lo = ex == 0u ? 0u : lo;
+    hi = ex == 255u ? (sign | 0x7ff00000u | (man ? 0x00080000u : 0u)) : hi;
+    lo = ex == 255u ? 0u : lo;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
 __device__ __forceinline__ bool is_finite(double x)
 {
     return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
@@ -155,6 +189,30 @@ __device__ __forceinline__ void stumpff_c2c3(double z, double& c2, double& c3)
     StumpffHorner<T - 2>::run(z, c2, c3);
 }
 
+// The same series in FP32 (coefficients 1/k! rounded to float), for the
+// Halley phase's starting point only.
+template <int K>
+struct StumpffHornerF {
+    static __device__ __forceinline__ void run(float z, float& c2, float& c3)
+    {
+        c2 = fmaf(-z, c2, (float)(1.0 / Factorial<2 * K + 2>::value));
+        c3 = fmaf(-z, c3, (float)(1.0 / Factorial<2 * K + 3>::value));
+        StumpffHornerF<K - 1>::run(z, c2, c3);
+    }
+};
+template <>
+struct StumpffHornerF<-1> {
+    static __device__ __forceinline__ void run(float, float&, float&) {}
+};
+
+template <int T>
+__device__ __forceinline__ void stumpff_c2c3_f32(float z, float& c2, float& c3)
+{
+    c2 = (float)(1.0 / Factorial<2 * T>::value);
+    c3 = (float)(1.0 / Factorial<2 * T + 1>::value);
+    StumpffHornerF<T - 2>::run(z, c2, c3);
+}
+
 
 // ------------------------------------------------------------------------
 // Kepler drift of one planet for time h under H_K,i (Sec. 3.2, Eq. 3),
@@ -168,12 +226,18 @@ __device__ __forceinline__ void stumpff_c2c3(double z, double& c2, double& c3)
 // steps with NT-term series.  The G_n at the final X = X1 + d come from the
 // values at the last Newton point X1 by one Taylor step (dG_n/dX = G_{n-1});
 // |d| is the last Newton correction, so the neglected d^2 terms are far below
-// rounding.  Then the Lagrange f - 1, g, fdot, gdot - 1.  No branches.
+// rounding.  Then the Lagrange f - 1, g, fdot, gdot - 1.
+// h32 (uniform across the warp) runs the initial guess and the Halley phase
+// in FP32: they only supply the Newton phase's starting point, and from a
+// start within ~1e-7 two FP64 Newton steps reach FP64 rounding
+// (quadratic convergence: 1e-7 -> 1e-14 -> rounding), so the result keeps
+// FP64 accuracy wherever the FP64 Halley phase converges, while ~60 FP64
+// operations per drift move to the FP32 pipe.  No other branches.
 // Returns beta > 0; Xout receives the final universal variable.
 template <int NT>
 __device__ __forceinline__ bool kepler_drift(double mu, double h, double& qx, double& qy,
                                              double& qz, double& vx, double& vy, double& vz,
-                                             double& Xout)
+                                             double& Xout, bool h32 = false)
 {
     const double r0sq = fma(qx, qx, fma(qy, qy, qz * qz));
     const double r0i = rsqrt(r0sq);
@@ -183,20 +247,41 @@ __device__ __forceinline__ bool kepler_drift(double mu, double h, double& qx, do
     const double beta = fma(2.0 * mu, r0i, -v2);
     const double zeta0 = fma(-beta, r0, mu);
     const double beta_eta0 = beta * eta0, beta_zeta0 = beta * zeta0;
-    const double hr = h * r0i;
-    double X = fma(-0.5 * eta0 * hr * hr, r0i, hr);
-    double X2, c2, c3, G2, G3;
+    double X, X2, c2, c3, G2, G3;
+    if (h32) {
+        const float r0f = to_f32(r0), r0if = to_f32(r0i), eta0f = to_f32(eta0);
+        const float zeta0f = to_f32(zeta0), betaf = to_f32(beta), hf = to_f32(h);
+        const float beta_eta0f = betaf * eta0f, beta_zeta0f = betaf * zeta0f;
+        const float hr = hf * r0if;
+        float Xs = fmaf(-0.5f * eta0f * hr * hr, r0if, hr);
 #pragma unroll
-    for (int it = 0; it < 2; ++it) {                 // Halley
-        X2 = X * X;
-        stumpff_c2c3<4>(beta * X2, c2, c3);
-        G2 = X2 * c2;
-        G3 = (X2 * X) * c3;
-        const double F = fma(r0, X, fma(eta0, G2, fma(zeta0, G3, -h)));
-        const double Fp = fma(zeta0, G2, fma(-beta_eta0, G3, fma(eta0, X, r0)));
-        const double Fpp = fma(-beta_zeta0, G3, fma(-beta_eta0, G2, fma(zeta0, X, eta0)));
-        const double den = fma(-0.5 * F, Fpp, Fp * Fp);          // (2F'^2 - F F'') / 2
-        X = fma(-(F * Fp), rcp(den), X);
+        for (int it = 0; it < 2; ++it) {             // Halley (FP32)
+            const float Y2 = Xs * Xs;
+            float s2, s3;
+            stumpff_c2c3_f32<4>(betaf * Y2, s2, s3);
+            const float H2 = Y2 * s2, H3 = (Y2 * Xs) * s3;
+            const float F = fmaf(r0f, Xs, fmaf(eta0f, H2, fmaf(zeta0f, H3, -hf)));
+            const float Fp = fmaf(zeta0f, H2, fmaf(-beta_eta0f, H3, fmaf(eta0f, Xs, r0f)));
+            const float Fpp = fmaf(-beta_zeta0f, H3, fmaf(-beta_eta0f, H2, fmaf(zeta0f, Xs, eta0f)));
+            const float den = fmaf(-0.5f * F, Fpp, Fp * Fp);
+            Xs = Xs - __fdividef(F * Fp, den);
+        }
+        X = to_f64(Xs);
+    } else {
+        const double hr = h * r0i;
+        X = fma(-0.5 * eta0 * hr * hr, r0i, hr);
+#pragma unroll
+        for (int it = 0; it < 2; ++it) {             // Halley
+            X2 = X * X;
+            stumpff_c2c3<4>(beta * X2, c2, c3);
+            G2 = X2 * c2;
+            G3 = (X2 * X) * c3;
+            const double F = fma(r0, X, fma(eta0, G2, fma(zeta0, G3, -h)));
+            const double Fp = fma(zeta0, G2, fma(-beta_eta0, G3, fma(eta0, X, r0)));
+            const double Fpp = fma(-beta_zeta0, G3, fma(-beta_eta0, G2, fma(zeta0, X, eta0)));
+            const double den = fma(-0.5 * F, Fpp, Fp * Fp);      // (2F'^2 - F F'') / 2
+            X = fma(-(F * Fp), rcp(den), X);
+        }
     }
     double d = 0.0;
 #pragma unroll
@@ -237,10 +322,11 @@ __device__ __forceinline__ bool kepler_drift(double mu, double h, double& qx, do
 
 template <int NT>
 __device__ __forceinline__ bool kepler_drift(double mu, double h, double& qx, double& qy,
-                                             double& qz, double& vx, double& vy, double& vz)
+                                             double& qz, double& vx, double& vy, double& vz,
+                                             bool h32 = false)
 {
     double X;
-    return kepler_drift<NT>(mu, h, qx, qy, qz, vx, vy, vz, X);
+    return kepler_drift<NT>(mu, h, qx, qy, qz, vx, vy, vz, X, h32);
 }
 
 // ------------------------------------------------------------------------
@@ -289,14 +375,47 @@ __device__ __forceinline__ double group_sum(const Group<L>& g, double x)
     }
 }
 
+// Sums of the 3-vector (x, y, z) over the system's lanes, the same bits in
+// every lane.  L = 4, 8: reduce-scatter of (x, y, z, 0) by xor partners
+// (keep half, send half: 2 + 1 (+ 1) additions per lane instead of 3 log2 L),
+// after which one lane pair holds each finished component (both lanes
+// compute a + b, which is commutative in IEEE arithmetic), then three
+// shuffles from those lanes give every lane the same values.  Other L:
+// three group_sum.
+template <int L>
+__device__ __forceinline__ void group_sum3(const Group<L>& g, double x, double y, double z,
+                                           double& sx, double& sy, double& sz)
+{
+    if (L == 4 || L == 8) {
+        constexpr int H = L / 2, Q = L / 4;
+        const bool hi = (g.p & H) != 0;          // keeps (z, 0), else (x, y)
+        double k0 = hi ? z : x, k1 = hi ? 0.0 : y;
+        const double s0 = hi ? x : z, s1 = hi ? y : 0.0;
+        k0 += __shfl_xor_sync(WHG_FULL_MASK, s0, H);
+        k1 += __shfl_xor_sync(WHG_FULL_MASK, s1, H);
+        const bool mid = (g.p & Q) != 0;         // keeps the second of the pair
+        double k = mid ? k1 : k0;
+        k += __shfl_xor_sync(WHG_FULL_MASK, mid ? k0 : k1, Q);
+        if (L == 8) k += __shfl_xor_sync(WHG_FULL_MASK, k, 1);
+        // lane base + 2*hi + mid (L = 4), base + 4*hi + 2*mid (+1) (L = 8)
+        // now holds component 2*hi + mid
+        sx = __shfl_sync(WHG_FULL_MASK, k, g.base);
+        sy = __shfl_sync(WHG_FULL_MASK, k, g.base + Q);
+        sz = __shfl_sync(WHG_FULL_MASK, k, g.base + H);
+    } else {
+        sx = group_sum<L>(g, x);
+        sy = group_sum<L>(g, y);
+        sz = group_sum<L>(g, z);
+    }
+}
+
 // Jump step (Sec. 3.4, Eq. 6): Q_i += (h/m0) sum_j m_j v_j; jc = h / m0.
 template <int L>
 __device__ __forceinline__ void jump(const Group<L>& g, double m, double jc, double vx, double vy,
                                      double vz, double& qx, double& qy, double& qz)
 {
-    const double px = group_sum<L>(g, m * vx);
-    const double py = group_sum<L>(g, m * vy);
-    const double pz = group_sum<L>(g, m * vz);
+    double px, py, pz;
+    group_sum3<L>(g, m * vx, m * vy, m * vz, px, py, pz);
     qx = fma(jc, px, qx);
     qy = fma(jc, py, qy);
     qz = fma(jc, pz, qz);
@@ -365,9 +484,8 @@ __device__ __forceinline__ bool kick(const Group<L>& g, double qx, double qy, do
             vz = fma(c, qz, vz);
         } else {
             const double ax = c * qx, ay = c * qy, az = c * qz;
-            const double bx = group_sum<L>(g, mrat * ax);
-            const double by = group_sum<L>(g, mrat * ay);
-            const double bz = group_sum<L>(g, mrat * az);
+            double bx, by, bz;
+            group_sum3<L>(g, mrat * ax, mrat * ay, mrat * az, bx, by, bz);
             vx = vx + (ax - bx);
             vy = vy + (ay - by);
             vz = vz + (az - bz);
@@ -522,6 +640,7 @@ __device__ __forceinline__ void step_body(const WhgState& st, const WhgBuckets& 
     const double jc = (0.5 * dt) / mu;
     const double mrat = m / mu;
     const double kgr = GRM ? (-6.0 * mu * mu * dt) / (st.c_light * st.c_light) : 0.0;
+    const bool h32 = st.halley32 != 0;
     // close-encounter distances of this lane's pairs (once per launch)
     double thr2[4] = {0.0, 0.0, 0.0, 0.0};
     {
@@ -545,7 +664,7 @@ __device__ __forceinline__ void step_body(const WhgState& st, const WhgBuckets& 
         const double hK = (nstep0 + done == 0) ? 0.5 * dt : dt;
         const double r0sq = fma(qx, qx, fma(qy, qy, qz * qz));
         const bool far = __double_as_longlong(r0sq) > __double_as_longlong(rej2);
-        const bool bound = kepler_drift<NT>(mu, hK, qx, qy, qz, vx, vy, vz);
+        const bool bound = kepler_drift<NT>(mu, hK, qx, qy, qz, vx, vy, vz, h32);
         bool close;
         if (GRM == 0 && st.merge) {                   // J(dt) I(dt): J and I commute without GR
             jump<L>(g, m, 2.0 * jc, vx, vy, vz, qx, qy, qz);
@@ -600,7 +719,7 @@ __device__ __forceinline__ void read_body(const WhgState& st, const WhgBuckets& 
     const double mu = pl.has_sys ? st.m0[s] : 1.0;
     const double dt = pl.has_sys ? st.dt[s] : 1.0e-3;
     const long long ns = pl.has_sys ? st.nstep[s] : 0;
-    if (ns > 0) kepler_drift<NT>(mu, 0.5 * dt, qx, qy, qz, vx, vy, vz);
+    if (ns > 0) kepler_drift<NT>(mu, 0.5 * dt, qx, qy, qz, vx, vy, vz, st.halley32 != 0);
     const double sqx = group_sum<L>(g, m * qx), sqy = group_sum<L>(g, m * qy), sqz = group_sum<L>(g, m * qz);
     const double spx = group_sum<L>(g, m * vx), spy = group_sum<L>(g, m * vy), spz = group_sum<L>(g, m * vz);
     if (!pl.has_sys) return;                         // after the last shuffle
@@ -650,7 +769,8 @@ __device__ __forceinline__ void energy_body(const WhgState& st, const WhgBuckets
     double vx = st.vx[lane], vy = st.vy[lane], vz = st.vz[lane];
     const double mu = pl.has_sys ? st.m0[s] : 1.0;
     const double dt = pl.has_sys ? st.dt[s] : 1.0e-3;
-    if (pl.has_sys && st.nstep[s] > 0) kepler_drift<NT>(mu, 0.5 * dt, qx, qy, qz, vx, vy, vz);
+    if (pl.has_sys && st.nstep[s] > 0)
+        kepler_drift<NT>(mu, 0.5 * dt, qx, qy, qz, vx, vy, vz, st.halley32 != 0);
     const double r2 = fma(qx, qx, fma(qy, qy, qz * qz));
     double pair = 0.0;
 #pragma unroll

@@ -25,6 +25,26 @@ __global__ void __launch_bounds__(256) k_dfma_loop(double* out, int iters, doubl
     out[tid] = s;
 }
 
+// The same loop with only the first `active` lanes of each warp working (the
+// others skip it): shows whether masked lanes cost FP64 pipe time.
+__global__ void k_dfma_lanes(double* out, int iters, int active)
+{
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    double a[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) a[j] = 1.0 + 1e-3 * (double)(tid + j);
+    if ((int)(threadIdx.x & 31u) < active) {
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int j = 0; j < kChains; ++j) a[j] = fma(a[j], 0.999999, 1e-9);
+        }
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) s += a[j];
+    out[tid] = s;
+}
+
 // Kepler drift with runtime iteration counts and series lengths, for the
 // solver search of Appendix A: 1/k! for k = 0..31 in constant memory; the
 // G_n after the last iteration are evaluated at the final X with the Newton
@@ -99,6 +119,8 @@ __global__ void k_special(const double* x, int n, double* out)
     out[n + i] = 1.0 / v;
     out[2 * n + i] = v > 0.0 ? whg::rsqrt(v) : 0.0;
     out[3 * n + i] = v > 0.0 ? ::rsqrt(v) : 0.0;
+    out[4 * n + i] = whg::to_f64(whg::to_f32(v));
+    out[5 * n + i] = (double)__double2float_rz(v);
 }
 
 }  // namespace
@@ -135,6 +157,33 @@ int whg_measure_fp64_tflops(double seconds, double* tflops)
     }
     if (rc == WHG_OK)
         *tflops = 2.0 * kChains * (double)iters * threads * blocks / (ms * 1e-3) / 1e12;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    return rc;
+}
+
+int whg_probe_fp64_lanes(int warps_per_sm, int active_lanes, int iters, float* ms)
+{
+    if (!ms || warps_per_sm < 1 || warps_per_sm > 64 || active_lanes < 1 || active_lanes > 32 ||
+        iters < 1 || iters > (1 << 24))
+        return WHG_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return WHG_ECUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return WHG_ECUDA;
+    const int blocks = sms * warps_per_sm;        // one warp per block
+    double* out = nullptr;
+    if (cudaMalloc(&out, sizeof(double) * 32 * (size_t)blocks) != cudaSuccess) return WHG_ENOMEM;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    k_dfma_lanes<<<blocks, 32>>>(out, 64, active_lanes);          // warm-up
+    cudaEventRecord(e0, 0);
+    k_dfma_lanes<<<blocks, 32>>>(out, iters, active_lanes);
+    cudaEventRecord(e1, 0);
+    int rc = WHG_OK;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) rc = WHG_ECUDA;
+    else cudaEventElapsedTime(ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(out);

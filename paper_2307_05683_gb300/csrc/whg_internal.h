@@ -34,6 +34,7 @@ struct WhgState {
     double hill;                     // close-encounter rule: mutual Hill radii (0 = off)
     double eject;                    // ejection rule: factor on the largest initial a (0 = off)
     int merge;                       // one J(dt) before I(dt) (GR off only)
+    int halley32;                    // Kepler solver: initial guess and Halley phase in FP32
 };
 
 // Bucket table (by value in every launch).

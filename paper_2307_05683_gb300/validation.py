@@ -34,8 +34,9 @@ def pericentre_timescale(a, e, mu=1.0):
     return 2 * np.pi / n * (1 - e) ** 2 / np.sqrt(1 - e * e)
 
 
-def accuracy_map(a_values, e_values, n_phases=8, years=10.0, dt_days=5.0, seed=0):
-    """Relative a error after `years` of massless particles (production kernel).
+def accuracy_map(a_values, e_values, n_phases=8, years=10.0, dt_days=5.0, seed=0, halley_fp32=False):
+    """Relative a error after `years` of massless particles (production kernel;
+    halley_fp32=True runs the solver's starting phase in FP32).
     Returns (err [na, ne, n_phases], status [na, ne, n_phases])."""
     a_values = np.asarray(a_values, float)
     e_values = np.asarray(e_values, float)
@@ -47,7 +48,7 @@ def accuracy_map(a_values, e_values, n_phases=8, years=10.0, dt_days=5.0, seed=0
     dt = dt_days * inputs.DAY
     n = int(round(years * 365.25 / dt_days))
     ens = inputs.test_particle(A.ravel(), E.ravel(), M.ravel(), dt=dt)
-    it = whg.Integrator(ens.n_systems, 1, gr_mode=0)
+    it = whg.Integrator(ens.n_systems, 1, gr_mode=0, halley_fp32=halley_fp32)
     it.init(ens)
     it.step(n)
     pos, vel, st, _ = it.read_state()
@@ -92,3 +93,36 @@ def default_search_grid():
         for ht in (range(2, 9) if hi else [4]):
             out.append((hi, ht, ni, nt))
     return out
+
+
+def solar_copies(n_systems: int, seed: int = 0, dt_days: float = 5.0, perturb_m: float = 1.0):
+    """One Solar-System-shaped system (the 8-planet template, angles from
+    `seed`) copied n_systems times, Mercury's x moved by +-perturb_m metres in
+    each copy (a random sign and size up to perturb_m), dt = dt_days."""
+    base = inputs.solar_ensemble(seed, 1)
+    rng = np.random.default_rng(seed + 1)
+    ens = base.tile(n_systems)
+    au_m = 1.495978707e11
+    ens.pos[:, 1, 0] += rng.uniform(-1.0, 1.0, n_systems) * perturb_m / au_m
+    ens.dt[:] = dt_days * inputs.DAY
+    return ens
+
+
+def energy_error_run(ens, total_steps: int, samples: int = 20, gr_mode: int = 1):
+    """Relative energy error |E(t)/E(0) - 1| of every system at `samples`
+    evenly spaced times (whg_energy on the synchronized state).
+    Returns (times [samples], errors [samples, S], status [S])."""
+    it = whg.Integrator(ens.n_systems, ens.max_planets, gr_mode=gr_mode)
+    it.init(ens)
+    E0 = it.energy()
+    chunk = max(1, total_steps // samples)
+    times, errs = [], []
+    done = 0
+    for _ in range(samples):
+        it.step(chunk)
+        done += chunk
+        times.append(done * float(ens.dt[0]))
+        errs.append(np.abs(it.energy() / E0 - 1.0))
+    _, _, st, _ = it.read_state()
+    it.close()
+    return np.asarray(times), np.asarray(errs), st

@@ -37,7 +37,8 @@ class whg_options(ctypes.Structure):
                 ("newton_terms", ctypes.c_int), ("lanes_per_system", ctypes.c_int),
                 ("block_size", ctypes.c_int), ("steps_per_launch", ctypes.c_longlong),
                 ("close_encounter_hill", ctypes.c_double), ("eject_factor", ctypes.c_double),
-                ("graph_launches", ctypes.c_int), ("merge_jumps", ctypes.c_int)]
+                ("graph_launches", ctypes.c_int), ("merge_jumps", ctypes.c_int),
+                ("halley_fp32", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -76,6 +77,8 @@ def load():
             "whg_destroy": (None, [P]),
             "whg_measure_fp64_tflops": (ctypes.c_int, [ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
             "whg_test_special": (ctypes.c_int, [D, ctypes.c_int, D]),
+            "whg_probe_fp64_lanes": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                    ctypes.POINTER(ctypes.c_float)]),
             "whg_kepler_sweep": (ctypes.c_int, [D, D, I, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                                 ctypes.c_longlong, D, D]),
             "whg_adjoint_forward": (ctypes.c_int, [P, ctypes.c_longlong, ctypes.c_int, D, D]),
@@ -99,7 +102,7 @@ def exported_symbols() -> list[str]:
             "whg_energy_device", "whg_get_raw", "whg_set_raw", "whg_synchronize",
             "whg_launch_count", "whg_last_error", "whg_destroy", "whg_measure_fp64_tflops",
             "whg_test_special", "whg_integrate_noalloc", "whg_adjoint_forward",
-            "whg_adjoint_backward", "whg_kepler_sweep"]
+            "whg_adjoint_backward", "whg_kepler_sweep", "whg_probe_fp64_lanes"]
 
 
 def _check(ctx, rc: int) -> None:
@@ -255,6 +258,14 @@ def whg_kepler_sweep(q, v, cfg, mu: float, h: float, steps: int, q_out, v_out) -
                                          _dev(v_out, "torch.float64")))
 
 
+def whg_probe_fp64_lanes(warps_per_sm: int, active_lanes: int, iters: int) -> float:
+    """Kernel time in ms of the FP64 lane probe (see whg.h)."""
+    ms = ctypes.c_float()
+    _check(None, load().whg_probe_fp64_lanes(int(warps_per_sm), int(active_lanes), int(iters),
+                                             ctypes.byref(ms)))
+    return float(ms.value)
+
+
 def whg_test_special(x, out) -> None:
     _check(None, load().whg_test_special(_dev(x, "torch.float64"), int(x.numel()),
                                          _dev(out, "torch.float64")))
@@ -286,7 +297,7 @@ class Integrator:
                  newton_terms: int = 8, lanes_per_system: int = 0, block_size: int = 0,
                  steps_per_launch: int = 0, close_encounter_hill: float = 0.0,
                  eject_factor: float = 0.0, graph_launches: int = 0, merge_jumps: bool = False,
-                 stream=None):
+                 halley_fp32: bool = False, stream=None):
         opt = whg_default_options()
         opt.gr_mode = gr_mode
         if c_light is not None:
@@ -299,6 +310,7 @@ class Integrator:
         opt.eject_factor = eject_factor
         opt.graph_launches = graph_launches
         opt.merge_jumps = int(merge_jumps)
+        opt.halley_fp32 = int(halley_fp32)
         self.S, self.N = int(n_systems), int(max_planets)
         self.stream = stream if stream is not None else current_stream()
         self.ctx = whg_create(self.S, self.N, opt, self.stream)

@@ -8,7 +8,24 @@ import pytest
 def test_alg_flops_table_matches_oracle_count(orc):
     bench = importlib.import_module("bench")
     for (n, nt, gr), flops in bench.ALG_FLOPS.items():
-        assert orc.count_flops(n, nt, gr)["flops"] == flops
+        c = orc.count_flops(n, nt, gr)
+        assert c["flops"] == flops
+        assert c["start_phase"] == bench.START_FLOPS[(n, nt, gr)]
+        assert bench.fp64_flops(gr, True, nt) == flops - c["start_phase"]
+        assert bench.fp64_flops(gr, False, nt) == flops
+
+
+def test_start_phase_count_follows_the_halley_iterations(orc):
+    """The starting-phase tally grows by one Halley step's flops per extra
+    iteration and is the initial guess alone without Halley steps, so it
+    covers exactly the guess and the Halley steps."""
+    c = [orc.count_flops(8, 8, 1, halley_iters=k) for k in range(4)]
+    per_step = c[1]["start_phase"] - c[0]["start_phase"]
+    assert per_step > 0 and c[0]["start_phase"] > 0                 # guess alone without Halley
+    assert all(c[k + 1]["start_phase"] - c[k]["start_phase"] == per_step for k in range(3))
+    # the rest of the step does not depend on the Halley iterations
+    assert len({x["flops"] - x["start_phase"] for x in c}) == 1
+    assert c[2]["start_phase"] % 8 == 0                             # same work in each of 8 drifts
 
 
 def test_fp64_peak_from_unit_counts():

@@ -58,5 +58,10 @@ def test_options_struct_layout(lib_path):
     assert o.gr_mode == 1 and o.newton_terms == 8
     assert o.c_light == pytest.approx(10065.32, rel=1e-5)
     assert o.close_encounter_hill == 0.0 and o.eject_factor == 0.0
-    assert o.graph_launches == 0 and o.merge_jumps == 0
-    assert ctypes.sizeof(whg.whg_options) == 64
+    assert o.graph_launches == 0 and o.merge_jumps == 0 and o.halley_fp32 == 0
+    assert ctypes.sizeof(whg.whg_options) == 72
+    # the library writes the last field: the C struct reaches as far as the ctypes one
+    s = whg.whg_options()
+    s.halley_fp32 = 12345
+    whg.load().whg_default_options(ctypes.byref(s))
+    assert s.halley_fp32 == 0

@@ -61,8 +61,9 @@ def _targets(ens, seed, spread=0.05):
     return T * live[..., None]
 
 
-@pytest.mark.parametrize("gr_mode,merge", [(0, False), (1, False), (2, False), (0, True)])
-def test_adjoint_matches_oracle_tangent(whg, orc, gr_mode, merge):
+@pytest.mark.parametrize("gr_mode,merge,h32", [(0, False, False), (1, False, False), (2, False, False),
+                                               (0, True, False), (1, False, True)])
+def test_adjoint_matches_oracle_tangent(whg, orc, gr_mode, merge, h32):
     """Every input direction of a few systems (8-planet and compact mixed),
     1000 steps, checkpoints every 100: the adjoint equals the oracle's
     forward-mode derivative to 1e-8 of the largest gradient entry."""
@@ -73,7 +74,8 @@ def test_adjoint_matches_oracle_tangent(whg, orc, gr_mode, merge):
                            np.concatenate([ens.n_planets, cmp.n_planets]), np.concatenate([ens.dt, cmp.dt]))
     T = _targets(both, 1)
     n = 1000
-    loss, gx, gu, gm = gpu_grad(whg, both, T, n, 100, gr_mode=gr_mode, merge_jumps=merge)
+    loss, gx, gu, gm = gpu_grad(whg, both, T, n, 100, gr_mode=gr_mode, merge_jumps=merge,
+                                  halley_fp32=h32)
     for s in range(both.n_systems):
         k = int(both.n_planets[s])
         L, tx, tu, tm = orc.tangent_gradient(both.masses[s], both.pos[s], both.vel[s], k, both.dt[s], T[s],

@@ -81,9 +81,9 @@ def test_own_rcp_rsqrt_against_cuda(whg):
                         10.0 ** rng.uniform(-6, 6, 200000),
                         1.0 + rng.uniform(-1e-9, 1e-9, 1000), [1.0, 2.0, 4.0, 0.5, 3.0]])
     xt = torch.tensor(x, dtype=torch.float64, device="cuda")
-    out = torch.empty(4 * x.size, dtype=torch.float64, device="cuda")
+    out = torch.empty(6 * x.size, dtype=torch.float64, device="cuda")
     whg.whg_test_special(xt, out)
-    r = out.cpu().numpy().reshape(4, -1)
+    r = out.cpu().numpy().reshape(6, -1)
     ulp_rcp = np.spacing(np.abs(r[1]))
     ulp_rsq = np.spacing(np.abs(r[3]))
     # CUDA's 1/x is correctly rounded; rsqrt is within 1 ulp of exact.
@@ -96,6 +96,42 @@ def test_own_rcp_rsqrt_against_cuda(whg):
     exact_rsq = 1 / np.sqrt(xl)
     err = np.abs(r[2][sel].astype(np.longdouble) - exact_rsq) / np.spacing(np.abs(r[3][sel]))
     assert float(err.max()) <= 1.5
+
+
+def test_own_fp32_conversions_against_cuda(whg):
+    """The integer-pipe FP64 -> FP32 -> FP64 round trip used for the Kepler
+    solver's FP32 starting phase: equal to CUDA's round-toward-zero
+    conversion in the FP32 normal range (and a truncation there by direct
+    check); signed zero below it, signed infinity above it and for inf/NaN."""
+    import torch
+    rng = np.random.default_rng(3)
+    mag = 10.0 ** rng.uniform(-45, 45, 200000)
+    x = np.concatenate([mag * rng.choice([-1.0, 1.0], mag.size),
+                        np.ldexp(1.0, np.arange(-130, 130)), -np.ldexp(1.0, np.arange(-130, 130)),
+                        np.nextafter(np.ldexp(1.0, np.arange(-126, 128)), 0.0),
+                        [0.0, -0.0, 1e-300, -1e-300, 1e300, -1e300, np.inf, -np.inf, np.nan,
+                         float(np.finfo(np.float32).max), float(np.finfo(np.float32).tiny)]])
+    xt = torch.tensor(x, dtype=torch.float64, device="cuda")
+    out = torch.empty(6 * x.size, dtype=torch.float64, device="cuda")
+    whg.whg_test_special(xt, out)
+    r = out.cpu().numpy().reshape(6, -1)
+    own, rz = r[4], r[5]
+    ax = np.abs(x)
+    normal = np.isfinite(x) & (ax >= 2.0 ** -126) & (ax < 2.0 ** 128)
+    assert np.array_equal(own[normal], rz[normal])
+    f = own[normal]
+    assert np.array_equal(f, f.astype(np.float32).astype(np.float64))          # FP32 values
+    assert np.all(np.signbit(f) == np.signbit(x[normal])) and np.all(np.abs(f) <= ax[normal])
+    gap = ax[normal] - np.abs(f)
+    with np.errstate(over="ignore"):                    # the spacing above FLT_MAX is inf
+        ulp = np.spacing(np.abs(f).astype(np.float32)).astype(np.float64)
+    assert np.all(gap < ulp)
+    tiny = np.isfinite(x) & (ax < 2.0 ** -126)
+    assert np.all(own[tiny] == 0.0) and np.array_equal(np.signbit(own[tiny]), np.signbit(x[tiny]))
+    big = ~np.isfinite(x) | (ax >= 2.0 ** 128)
+    assert np.all(np.isinf(own[big]))
+    fin_big = big & ~np.isnan(x)
+    assert np.array_equal(np.signbit(own[fin_big]), np.signbit(x[fin_big]))
 
 
 # ------------------------------------------------------------- parity --
@@ -433,3 +469,33 @@ def test_merged_jumps_match_oracle(whg, orc, n, tol):
     s = inputs.solar_ensemble(13, 64)
     assert_parity(gpu_run(whg, s, 500, gr_mode=0, merge_jumps=True),
                   oracle_run(orc, s, 500, gr_mode=0, merge_jumps=True), 1e-11, s.n_planets)
+
+
+@pytest.mark.parametrize("case", ["two_planet_1", "two_planet_1e4", "solar_1", "solar_1e4", "compact",
+                                  "particles", "status"])
+def test_halley_fp32_matches_oracle(whg, orc, case):
+    """halley_fp32 = 1: the Kepler solver's initial guess and Halley phase in
+    FP32 (FP64 Newton phase), against the all-FP64 oracle at the same
+    tolerances as the default all-FP64 path."""
+    if case.startswith("two_planet"):
+        ens, gr = inputs.two_planet_system(0, 10), 0
+        n, tol = (1, 1e-12) if case.endswith("_1") else (10000, 1e-9)
+    elif case.startswith("solar"):
+        ens, gr = inputs.solar_ensemble(2, 256), 1
+        n, tol = (1, 1e-12) if case.endswith("_1") else (10000, 1e-9)
+    elif case == "compact":
+        ens, n, tol, gr = inputs.compact_ensemble(5, 200), 500, 1e-10, 1
+    elif case == "particles":
+        ens = inputs.test_particle(np.linspace(0.3, 2.0, 40), np.linspace(0.0, 0.6, 40), np.linspace(0, 6, 40))
+        n, tol, gr = 3000, 1e-10, 0
+    else:
+        ens = inputs.two_planet_system(3, 4)
+        ens.vel[1, 2] *= 3.0
+        ens.pos[2, 2] = ens.pos[2, 1]
+        ens.vel[2, 2] = ens.vel[2, 1]
+        n, tol, gr = 50, 1e-12, 0
+    g = gpu_run(whg, ens, n, gr_mode=gr, halley_fp32=True)
+    o = oracle_run(orc, ens, n, gr_mode=gr)
+    assert_parity(g, o, tol, ens.n_planets)
+    if case == "status":
+        assert list(g[2]) == [0, 2, 1, 0]

@@ -71,3 +71,15 @@ def test_autotuner_picks_a_valid_configuration_and_caches_it(whg, tmp_path):
     sx = np.abs(ref[0]).max(axis=(1, 2))[:, None, None]
     assert np.array_equal(st, ref[2])
     assert (np.abs(p - ref[0]) / sx).max() <= 1e-12
+
+
+def test_fp64_masked_lanes_cost_full_pipe_time():
+    """The lane layout fills all 32 lanes of a warp with planets (floor(32/L)
+    systems per warp) rather than spreading a small ensemble over more,
+    partly filled warps: on this GPU an FP64 warp instruction takes the same
+    pipe time whatever the number of active lanes."""
+    from paper_2307_05683_gb300 import build, whg
+    build.build()
+    t32 = whg.whg_probe_fp64_lanes(4, 32, 4000)
+    t8 = whg.whg_probe_fp64_lanes(4, 8, 4000)
+    assert t32 > 0 and t8 >= 0.9 * t32, (t8, t32)

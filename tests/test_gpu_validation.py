@@ -67,3 +67,44 @@ def test_iteration_search_matches_oracle(val, orc):
         assert (res[c] < 1e-13) == (worst < 1e-13), (c, res[c], worst)
         assert abs(res[c] - worst) <= 2e-14 + 1e-2 * worst, (c, res[c], worst)
     assert res[(2, 4, 2, 8)] < 1e-13 and res[(2, 4, 1, 8)] > 1e-13
+
+
+def test_energy_error_run_matches_oracle(val, orc):
+    """The long-term energy tool (Sec. 5 experiment) on 32 perturbed copies:
+    |E(t)/E0 - 1| at each sample equals the oracle's on the same copies."""
+    ens = val.solar_copies(32, seed=2)
+    assert np.all(ens.pos[:, 2:] == ens.pos[:1, 2:]) and np.all(ens.vel == ens.vel[:1])
+    d = np.abs(ens.pos[:, 1, 0] - ens.pos[0, 1, 0]) * 1.495978707e11
+    assert d.max() <= 2.0 + 1e-3 and np.unique(ens.pos[:, 1, 0]).size == 32
+    times, errs, st = val.energy_error_run(ens, 20000, samples=4, gr_mode=1)
+    assert np.all(st == 0) and errs.shape == (4, 32)
+    assert np.allclose(times, np.arange(1, 5) * 5000 * ens.dt[0], rtol=1e-15)
+    o = orc.OracleEnsemble(32, 8, gr_mode=1)
+    o.init(ens)
+    E0 = o.energy()
+    for k in range(4):
+        o.run_threads(5000, 8)
+        ref = np.abs(o.energy() / E0 - 1.0)
+        assert np.all(np.abs(errs[k] - ref) <= 1e-11 + 1e-3 * ref), (k, errs[k] - ref)
+    assert np.median(errs) < 1e-7
+
+
+def test_accuracy_map_with_fp32_halley_phase(val):
+    """Fig. 1 map with the FP32 Halley phase (option) against the all-FP64
+    solver (default): inside the solver's domain
+    (pericentre timescale >= 2 steps, Eq. 4) the same statuses and the same
+    errors to rounding as the all-FP64 solver, and machine precision where
+    the pericentre timescale is resolved."""
+    a = [0.1, 0.2, 0.387, 0.6, 1.0]
+    e = [0.0, 0.2, 0.4, 0.6, 0.65, 0.7, 0.8, 0.9]
+    ref, st_ref = val.accuracy_map(a, e, n_phases=4, seed=9, halley_fp32=False)
+    got, st = val.accuracy_map(a, e, n_phases=4, seed=9, halley_fp32=True)
+    A, E = np.meshgrid(a, e, indexing="ij")
+    T = np.repeat(val.pericentre_timescale(A, E)[..., None], 4, axis=2)
+    dom = T >= 2 * 5 * inputs.DAY
+    assert np.array_equal(st[dom], st_ref[dom])
+    ok = dom & (st == 0)
+    assert np.all(np.abs(got[ok] - ref[ok]) <= 1e-13 + 1e-9 * np.abs(ref[ok]))
+    conv = (A >= 0.387) & (E <= 0.6)
+    conv = np.repeat(conv[..., None], 4, axis=2)
+    assert np.all(np.abs(got[conv]) < 1e-13)
