@@ -206,6 +206,25 @@ class ClockSampler:
 
 # ------------------------------------------------------------ CPU oracle --
 
+def cpu_model() -> str:
+    """Host CPU model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
 def oracle_rate(ens, gr_mode: int, target_cpu_seconds: float, threads: int):
     """Time the oracle (as it stands) on `threads` host threads over a bounded
     sample of the ensemble: all systems, a step count sized for about
@@ -295,6 +314,41 @@ def time_rate(whg, torch, ens, window_s: float, stream, **kw) -> tuple[float, in
         return S * n / (e0.elapsed_time(e1) / 1e3), n
     finally:
         it.close()
+
+
+def measure_uneven(whg, torch, systems=1 << 16, steps=20000, seed=303):
+    """Uneven batch: compact systems with 2..8 planets in one ensemble, both
+    stop rules on (a pair closer than 1 mutual Hill radius, a planet beyond
+    100x the largest initial a), 100-step launches replayed as CUDA graphs of
+    16, GR on.  Systems packed by planet count (n lanes each, 8 for n = 7)
+    against 8 lanes for every system, and packed with stopped systems
+    regrouped behind running ones after every graph replay (repack_frozen).
+    Rates count every system for every
+    step (a frozen system counts but costs nothing once its whole warp is
+    frozen); CUDA events on the library's stream after a warm-up of 1600
+    steps."""
+    ens = inputs.compact_ensemble(seed, systems)
+    stream = torch.cuda.Stream()
+    out = {"workload": f"{systems} compact systems, 2..8 planets, stop rules on (1 mutual Hill radius, "
+                       f"100 x largest initial a), GR on, 100-step launches in graphs of 16, {steps} steps"}
+    for name, lanes, repack in (("packed", 0, False), ("lanes8", 8, False), ("packed_repack", 0, True)):
+        it = whg.Integrator(systems, 8, gr_mode=1, lanes_per_system=lanes, steps_per_launch=100,
+                            graph_launches=16, close_encounter_hill=1.0, eject_factor=100.0,
+                            repack_frozen=repack, stream=stream.cuda_stream)
+        it.init(ens)
+        it.step(1600)
+        it.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        _, _, st, _ = it.read_state()
+        it.close()
+        out[name] = {"system_steps_per_s": round(systems * steps / (ms / 1e3), 1),
+                     "stopped": int((st != 0).sum())}
+    return out
 
 
 def throughput_sweep(whg, torch, sizes=tuple(1 << k for k in range(14, 21)), window_s=0.4, seed=77):
@@ -422,6 +476,7 @@ def run_whg(args):
     adjoint = measure_adjoint(whg, torch) if world == 1 else None
     sweep = throughput_sweep(whg, torch) if world == 1 else None
     solvers = solver_comparison(whg, torch, ens, args.gr_mode) if world == 1 else None
+    uneven = measure_uneven(whg, torch) if world == 1 else None
     roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                 "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
                 "traffic": profiled_traffic(),
@@ -444,6 +499,7 @@ def run_whg(args):
             "adjoint": adjoint,
             "sweep": sweep,
             "solver_comparison": solvers,
+            "uneven_batch": uneven,
             "clocks": clock_info,
             "systems_flagged": bad}
     it.close()
@@ -451,7 +507,8 @@ def run_whg(args):
         threads = os.cpu_count() or 1
         rate, sample, used = oracle_rate(ens, args.gr_mode, args.cpu_seconds, threads)
         line["cpu_baseline"] = {"value": round(rate, 1), "unit": UNIT, "cores": used, "kind": "oracle",
-                                "sample": sample}
+                                "sample": sample, "per_core": round(rate / max(used, 1), 1),
+                                "cpu_model": cpu_model()}
     if dist:
         dist.destroy_process_group()
     print(json.dumps(line), flush=True)
@@ -492,7 +549,8 @@ def run_reference(args):
             "data": "synthetic (seeded Solar-System-shaped ensemble)", "config": workload(args),
             "note": "the oracle runs the whole Kepler solver in FP64",
             "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "per_core": round(value / max(threads, 1), 1),
+                             "cpu_model": cpu_model()},
             "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

@@ -107,6 +107,17 @@ typedef struct {
                                  (pericentre timescale below ~2 steps) both are inaccurate and
                                  may stop differently.  Default 0: the whole solver in FP64
                                  (the paper's arithmetic). */
+    int repack_frozen;        /* 1: every graph_launches step launches (every 16 without
+                                 graphs; inside the captured graph with them) regroup the
+                                 systems of each planet count so that running systems come
+                                 first and stopped ones (status != 0) last.  A warp whose
+                                 systems have all stopped skips its steps, so stopped
+                                 systems stop costing time.  Each system's arithmetic uses
+                                 only its own lanes: results are bitwise those without
+                                 repacking.  Costs a second copy of the state in device
+                                 memory (allocated by whg_create).  Not part of the
+                                 paper's method.  Ignored by whg_integrate_noalloc.
+                                 Default 0. */
 } whg_options;
 
 /* Fill *opt with the defaults above. */

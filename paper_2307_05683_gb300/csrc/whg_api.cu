@@ -43,6 +43,13 @@ struct whg_ctx {
     cudaStream_t capture;
     cudaGraphExec_t graph;
     long long graph_chunk;
+    // repacking (opt.repack_frozen): a mirror of the state block and the order
+    void* state_base;
+    size_t state_bytes;
+    void* repack_buf;
+    WhgState scratch;
+    int* order;
+    long long since_repack;   // step launches since the last repack
     char err[256];
 };
 
@@ -174,6 +181,43 @@ int validate(const whg_ctx* c, const double* m, const double* x, const double* u
     return -1;
 }
 
+// Point the fields of st into one state block (lane arrays: L entries each,
+// per-system arrays: P); returns the block's [P] int region after status
+// (the internal -> caller map).
+int* carve_state(WhgState& st, void* base, size_t L, size_t P)
+{
+    double* d = (double*)base;
+    st.m = d; d += L;
+    st.qx = d; d += L;
+    st.qy = d; d += L;
+    st.qz = d; d += L;
+    st.vx = d; d += L;
+    st.vy = d; d += L;
+    st.vz = d; d += L;
+    st.a0 = d; d += L;
+    st.m0 = d; d += P;
+    st.dt = d; d += P;
+    st.M = d; d += P;
+    st.xcm = d; d += 3 * P;
+    st.vcm = d; d += 3 * P;
+    st.rej2 = d; d += P;
+    long long* ll = (long long*)d;
+    st.nstep = ll; ll += P;
+    int* ip = (int*)ll;
+    st.nplan = ip; ip += P;
+    st.status = ip; ip += P;
+    return ip;
+}
+
+// Repack on `stream`: live systems first in every bucket, through the mirror
+// block, copied back so that every pointer (and captured graph) stays valid.
+cudaError_t enqueue_repack(whg_ctx* c, cudaStream_t stream)
+{
+    cudaError_t e = whg_launch_repack(c->st, c->scratch, c->bk, c->order, stream);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(c->state_base, c->repack_buf, c->state_bytes, cudaMemcpyDeviceToDevice, stream);
+}
+
 int launch_check(whg_ctx* c, cudaError_t e, const char* what)
 {
     if (e != cudaSuccess) return cuda_fail(c, e, what);
@@ -201,6 +245,7 @@ void whg_default_options(whg_options* opt)
     opt->graph_launches = 0;
     opt->merge_jumps = 0;
     opt->halley_fp32 = 0;
+    opt->repack_frozen = 0;
 }
 
 int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options* opt_in,
@@ -234,6 +279,8 @@ int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options*
         return fail(nullptr, WHG_EINVAL, "steps_per_launch=%lld must be >= 0", opt.steps_per_launch);
     if (opt.graph_launches < 0 || opt.graph_launches > 4096)
         return fail(nullptr, WHG_EINVAL, "graph_launches=%d must be in 0..4096", opt.graph_launches);
+    if (opt.repack_frozen != 0 && opt.repack_frozen != 1)
+        return fail(nullptr, WHG_EINVAL, "repack_frozen=%d must be 0 or 1", opt.repack_frozen);
 
     whg_ctx* c = new (std::nothrow) whg_ctx();
     if (!c) return fail(nullptr, WHG_ENOMEM, "host allocation failed");
@@ -259,29 +306,23 @@ int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options*
         delete c;
         return fail(nullptr, WHG_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
     }
-    double* d = (double*)base;
+    c->state_base = base;
+    c->state_bytes = bytes;
     WhgState& st = c->st;
-    st.m = d; d += L;
-    st.qx = d; d += L;
-    st.qy = d; d += L;
-    st.qz = d; d += L;
-    st.vx = d; d += L;
-    st.vy = d; d += L;
-    st.vz = d; d += L;
-    st.a0 = d; d += L;
-    st.m0 = d; d += P;
-    st.dt = d; d += P;
-    st.M = d; d += P;
-    st.xcm = d; d += 3 * P;
-    st.vcm = d; d += 3 * P;
-    st.rej2 = d; d += P;
-    long long* ll = (long long*)d;
-    st.nstep = ll; ll += P;
-    int* ip = (int*)ll;
-    st.nplan = ip; ip += P;
-    st.status = ip; ip += P;
-    c->perm_d = ip;
+    c->perm_d = carve_state(st, base, L, P);
     st.perm = nullptr;
+    if (opt.repack_frozen) {                             // mirror block + order array
+        e = cudaMalloc(&c->repack_buf, bytes + P * sizeof(int));
+        if (e != cudaSuccess) {
+            cudaFree(base);
+            delete c;
+            return fail(nullptr, WHG_ENOMEM, "cudaMalloc(%zu): %s", bytes + P * sizeof(int),
+                        cudaGetErrorString(e));
+        }
+        c->scratch.perm = carve_state(c->scratch, c->repack_buf, L, P);
+        c->scratch.S = n_systems;
+        c->order = (int*)((char*)c->repack_buf + bytes);
+    }
     st.S = n_systems;
     st.Nmax = max_planets;
     st.c_light = opt.c_light;
@@ -298,6 +339,7 @@ int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options*
     e = cudaMalloc(&sbase, sbytes);
     if (e != cudaSuccess) {
         cudaFree(base);
+        if (c->repack_buf) cudaFree(c->repack_buf);
         delete c;
         return fail(nullptr, WHG_ENOMEM, "cudaMalloc(%zu): %s", sbytes, cudaGetErrorString(e));
     }
@@ -323,7 +365,7 @@ static int init_common(whg_ctx* c, const WhgIn& in, const int* nplan_host)
     const bool permuted = plan_layout(c->S, c->Nmax, c->Lfixed, nplan_host, &c->bk, perm.data());
     if (c->bk.warp0[c->bk.nb] > c->warps_cap)
         return fail(c, WHG_EINVAL, "internal layout exceeds capacity");
-    if (permuted) {
+    if (permuted || c->repack_buf) {                     // repacking needs the map even if identity
         WHG_CUDA(c, cudaMemcpyAsync(c->perm_d, perm.data(), perm.size() * sizeof(int),
                                     cudaMemcpyHostToDevice, c->stream));
         c->st.perm = c->perm_d;
@@ -335,6 +377,7 @@ static int init_common(whg_ctx* c, const WhgIn& in, const int* nplan_host)
     c->initialized = true;
     c->host_nstep = 0;
     c->adj_ready = false;
+    c->since_repack = 0;
     if (c->graph) {                                      // kernel arguments changed: capture again
         cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;
@@ -413,6 +456,7 @@ int whg_step(whg_ctx* c, long long n)
             cudaError_t e = cudaSuccess;
             for (long long i = 0; i < G && e == cudaSuccess; ++i)
                 e = whg_launch_step(c->st, c->bk, chunk, c->opt.newton_terms, c->opt.gr_mode, cl);
+            if (e == cudaSuccess && c->repack_buf) e = enqueue_repack(c, c->capture);   // once per replay
             cudaGraph_t graph = nullptr;
             const cudaError_t e2 = cudaStreamEndCapture(c->capture, &graph);
             if (e != cudaSuccess) return cuda_fail(c, e, "step kernel (capture)");
@@ -427,16 +471,23 @@ int whg_step(whg_ctx* c, long long n)
         }
         while (n >= G * chunk) {                          // replay on the context's stream
             WHG_CUDA(c, cudaGraphLaunch(c->graph, c->stream));
-            c->launches += G;
+            c->launches += G + (c->repack_buf ? 2 : 0);
+            if (c->repack_buf) c->since_repack = 0;
             n -= G * chunk;
         }
     }
+    const long long every = G > 0 ? G : 16;              // step launches between repacks
     while (n > 0) {
         const long long k = n < chunk ? n : chunk;
         int rc = launch_check(c, whg_launch_step(c->st, c->bk, k, c->opt.newton_terms, c->opt.gr_mode, l),
                               "step kernel");
         if (rc) return rc;
         n -= k;
+        if (c->repack_buf && ++c->since_repack >= every) {
+            WHG_CUDA(c, enqueue_repack(c, c->stream));
+            c->launches += 2;
+            c->since_repack = 0;
+        }
     }
     return WHG_OK;
 }
@@ -683,6 +734,7 @@ void whg_destroy(whg_ctx* c)
     cudaStreamSynchronize(c->stream);
     cudaFree(c->st.m);
     cudaFree(c->stage_d);
+    if (c->repack_buf) cudaFree(c->repack_buf);
     if (c->adj_buf) cudaFree(c->adj_buf);
     if (c->side) {
         cudaStreamSynchronize(c->side);

@@ -92,6 +92,10 @@ struct WhgLaunch {
 
 // Kernel launchers (whg_kernels_common.cu, whg_kernels_nt6.cu, whg_kernels_nt8.cu).
 cudaError_t whg_launch_init(const WhgState&, const WhgBuckets&, const WhgIn&, const WhgLaunch&);
+// Repack (live systems first in every bucket) into `scratch` (same layout as
+// st; order: S ints of scratch space); the caller copies scratch back.
+cudaError_t whg_launch_repack(const WhgState& st, const WhgState& scratch, const WhgBuckets& bk, int* order,
+                              cudaStream_t stream);
 cudaError_t whg_launch_raw(const WhgState&, const WhgBuckets&, const WhgOut&, int set, const WhgLaunch&);
 cudaError_t whg_launch_step(const WhgState&, const WhgBuckets&, long long nsteps, int newton_terms,
                             int gr_mode, const WhgLaunch&);

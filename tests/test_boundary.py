@@ -63,5 +63,6 @@ def test_options_struct_layout(lib_path):
     # the library writes the last field: the C struct reaches as far as the ctypes one
     s = whg.whg_options()
     s.halley_fp32 = 12345
+    s.repack_frozen = 6789
     whg.load().whg_default_options(ctypes.byref(s))
-    assert s.halley_fp32 == 0
+    assert s.halley_fp32 == 0 and s.repack_frozen == 0

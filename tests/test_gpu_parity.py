@@ -384,6 +384,32 @@ def test_energy_error_statistics_match(whg, orc):
     assert np.abs(dEg).max() < 1e-6
 
 
+def test_energy_error_distributions_match_on_compact_systems(whg, orc):
+    """512 compact systems (2-8 planets, 8-12 mutual Hill radii) over 5e4
+    steps.  Many of them are chaotic, so per-system values from the GPU and
+    the oracle may separate, but the distributions of log10 |E/E0 - 1| over
+    the systems both leave running agree (two-sample Kolmogorov-Smirnov)."""
+    stats = pytest.importorskip("scipy.stats")
+    ens = inputs.compact_ensemble(21, 512)
+    it = whg.Integrator(512, 8, gr_mode=1)
+    it.init(ens)
+    E0 = it.energy()
+    it.step(50000)
+    st = it.read_state()[2]
+    dEg = it.energy() / E0 - 1
+    it.close()
+    o = orc.OracleEnsemble(512, 8, gr_mode=1)
+    o.init(ens)
+    E0o = o.energy()
+    o.run_threads(50000, CORES)
+    sto = o.read_state()[2]
+    dEo = o.energy() / E0o - 1
+    ok = (st == 0) & (sto == 0) & np.isfinite(dEg) & np.isfinite(dEo) & (dEg != 0) & (dEo != 0)
+    assert ok.sum() >= 450
+    res = stats.ks_2samp(np.log10(np.abs(dEg[ok])), np.log10(np.abs(dEo[ok])))
+    assert res.pvalue > 0.01, res
+
+
 # ------------------------------------------------------------ stop rules --
 
 def test_ejection_stop_step_matches_oracle(whg, orc):
@@ -499,3 +525,37 @@ def test_halley_fp32_matches_oracle(whg, orc, case):
     assert_parity(g, o, tol, ens.n_planets)
     if case == "status":
         assert list(g[2]) == [0, 2, 1, 0]
+
+
+def test_uneven_batch_full_size_sampled(whg, orc):
+    """65,536 compact systems with 2..8 planets in one ensemble, both stop
+    rules on (a pair closer than 1 mutual Hill radius, a planet beyond 100x
+    the largest initial a), in the launch configuration the benchmark times
+    (100-step launches replayed as CUDA graphs of 16).  400 steps; 512
+    sampled systems checked one by one against the oracle (statuses, stop
+    steps, states to 1e-10)."""
+    S = 1 << 16
+    ens = inputs.compact_ensemble(303, S)
+    kw = dict(close_encounter_hill=1.0, eject_factor=100.0)
+    it = whg.Integrator(S, 8, gr_mode=1, steps_per_launch=100, graph_launches=16, **kw)
+    it.init(ens)
+    it.step(400)
+    pos, vel, st, t = it.read_state()
+    Q, v, ns, _ = it.get_raw()
+    it.close()
+    rng = np.random.default_rng(5)
+    idx = np.sort(rng.choice(S, 512, replace=False))
+    sub = ens.subset(idx)
+    o = orc.OracleEnsemble(512, 8, gr_mode=1, encounter_hill=1.0, eject_factor=100.0)
+    o.init(sub)
+    o.run_threads(400, CORES)
+    ref = o.read_state() + o.get_raw() + (o.energy(),)
+    it2 = whg.Integrator(512, 8, gr_mode=1, **kw)        # the same systems alone, for the energy
+    it2.init(sub)
+    it2.step(400)
+    E = it2.energy()
+    it2.close()
+    g = (pos[idx], vel[idx], st[idx], t[idx], Q[idx], v[idx], ns[idx], None, E)
+    assert_parity(g, ref, 1e-10, sub.n_planets)
+    assert set(np.unique(st)) <= {0, whg.WHG_STATUS_CLOSE_ENCOUNTER, whg.WHG_STATUS_EJECTED,
+                                  whg.WHG_STATUS_CLOSE_ENCOUNTER | whg.WHG_STATUS_EJECTED}
