@@ -51,11 +51,21 @@ __device__ __forceinline__ double stumpff_c(double z)
 // Adjoint of one Kepler drift (Q0, v0) -> (Q1, v1) for time h, mu = G m0,
 // final universal variable X.  In: lq, lv = adjoints of Q1, v1.  Out: lq, lv
 // = adjoints of Q0, v0; lmu accumulates the adjoint of mu.
+//
+// c4, c5 come from their NT-term series and c2 = 1/2 - z c4, c3 = 1/6 - z c5
+// from the recurrence (one more term of c2, c3 than the forward drift sums:
+// a change of ~z^NT/(2NT+2)!, far below the gradient's accuracy).  Every
+// Lagrange coefficient is mu times a function of the G_n, so the adjoints of
+// mu, r, r0 and G_n are written with f - 1, fdot and gdot - 1 themselves:
+//   mub  = ((f-1) fb + fdot fdb + (gdot-1) gdb) / mu - G3 gb,
+//   rb   = -((fdot fdb + (gdot-1) gdb) / r,   r0b = -((f-1) fb + fdot fdb) / r0,
+//   G1b  = -(mu / (r r0)) fdb,  G2b = -(mu / r0) fb - (mu / r) gdb,  G3b = -mu gb,
+// with fb = lq.Q0, gb = lq.v0, fdb = lv.Q0, gdb = lv.v0.
 template <int NT>
-__device__ __forceinline__ void kepler_vjp(double mu, double h, double qx, double qy, double qz,
-                                           double vx, double vy, double vz, double X, double& lqx,
-                                           double& lqy, double& lqz, double& lvx, double& lvy,
-                                           double& lvz, double& lmu)
+__device__ __forceinline__ void kepler_vjp(double mu, double muinv, double h, double qx, double qy,
+                                           double qz, double vx, double vy, double vz, double X,
+                                           double& lqx, double& lqy, double& lqz, double& lvx,
+                                           double& lvy, double& lvz, double& lmu)
 {
     const double r0sq = fma(qx, qx, fma(qy, qy, qz * qz));
     const double r0i = rsqrt(r0sq);
@@ -63,57 +73,62 @@ __device__ __forceinline__ void kepler_vjp(double mu, double h, double qx, doubl
     const double eta0 = fma(qx, vx, fma(qy, vy, qz * vz));
     const double v2 = fma(vx, vx, fma(vy, vy, vz * vz));
     const double beta = fma(2.0 * mu, r0i, -v2);
-    const double X2 = X * X;
+    const double X2 = X * X, X4 = X2 * X2;
     const double z = beta * X2;
-    const double c2 = stumpff_c<2, NT>(z), c3 = stumpff_c<3, NT>(z);
     const double c4 = stumpff_c<4, NT>(z), c5 = stumpff_c<5, NT>(z);
-    const double G2 = X2 * c2, G3 = X2 * X * c3, G4 = X2 * X2 * c4, G5 = X2 * X2 * X * c5;
+    const double c2 = fma(-z, c4, 0.5), c3 = fma(-z, c5, 1.0 / 6.0);
+    const double G2 = X2 * c2, G3 = (X2 * X) * c3, G4 = X4 * c4, G5 = (X4 * X) * c5;
     const double G0 = fma(-beta, G2, 1.0), G1 = fma(-beta, G3, X);
     const double r = fma(r0, G0, fma(eta0, G1, mu * G2));
     const double ri = rcp(r);
-    const double f = fma(-mu * r0i, G2, 1.0), g = fma(-mu, G3, h);
-    const double fd = -(mu * ri * r0i) * G1, gd = fma(-mu * ri, G2, 1.0);
+    const double A = mu * r0i, B = mu * ri, C = A * ri;
+    const double fm1 = -A * G2, g = fma(-mu, G3, h), fd = -C * G1, gdm1 = -B * G2;
     // (a) outputs Q1 = f Q0 + g v0, v1 = fd Q0 + gd v0
-    const double fb = lqx * qx + lqy * qy + lqz * qz;
-    const double gb = lqx * vx + lqy * vy + lqz * vz;
-    const double fdb = lvx * qx + lvy * qy + lvz * qz;
-    const double gdb = lvx * vx + lvy * vy + lvz * vz;
-    double nqx = f * lqx + fd * lvx, nqy = f * lqy + fd * lvy, nqz = f * lqz + fd * lvz;
-    double nvx = g * lqx + gd * lvx, nvy = g * lqy + gd * lvy, nvz = g * lqz + gd * lvz;
-    // (b) f - 1 = -mu G2/r0, g = h - mu G3, fd = -mu G1/(r r0), gd - 1 = -mu G2/r
-    double mub = -fb * G2 * r0i - gb * G3 - fdb * G1 * ri * r0i - gdb * G2 * ri;
-    double G1b = -fdb * mu * ri * r0i;
-    double G2b = -fb * mu * r0i - gdb * mu * ri;
-    const double G3b = -gb * mu;
-    const double rb = fdb * mu * G1 * ri * ri * r0i + gdb * mu * G2 * ri * ri;
-    double r0b = fb * mu * G2 * r0i * r0i + fdb * mu * G1 * ri * r0i * r0i;
+    const double fb = fma(lqx, qx, fma(lqy, qy, lqz * qz));
+    const double gb = fma(lqx, vx, fma(lqy, vy, lqz * vz));
+    const double fdb = fma(lvx, qx, fma(lvy, qy, lvz * qz));
+    const double gdb = fma(lvx, vx, fma(lvy, vy, lvz * vz));
+    const double f = 1.0 + fm1, gd = 1.0 + gdm1;
+    double nqx = fma(f, lqx, fd * lvx), nqy = fma(f, lqy, fd * lvy), nqz = fma(f, lqz, fd * lvz);
+    double nvx = fma(g, lqx, gd * lvx), nvy = fma(g, lqy, gd * lvy), nvz = fma(g, lqz, gd * lvz);
+    // (b) through f, g, fd, gd
+    const double tf = fm1 * fb, tfd = fd * fdb, tgd = gdm1 * gdb;
+    double mub = fma(tf + tfd + tgd, muinv, -G3 * gb);
+    const double rb = -(tfd + tgd) * ri;
+    double r0b = -(tf + tfd) * r0i;
+    double G1b = -C * fdb;
+    double G2b = fma(-A, fb, -B * gdb);
+    const double G3b = -mu * gb;
     // (c) r = r0 G0 + eta0 G1 + mu G2
-    r0b += rb * G0;
+    r0b = fma(rb, G0, r0b);
     double eta0b = rb * G1;
-    mub += rb * G2;
+    mub = fma(rb, G2, mub);
     const double G0b = rb * r0;
-    G1b += rb * eta0;
-    G2b += rb * mu;
-    // (d) G_n(beta, X)
-    const double dG0 = -0.5 * X * G1, dG1 = 0.5 * (G3 - X * G2);
-    const double dG2 = 0.5 * (2.0 * G4 - X * G3), dG3 = 0.5 * (3.0 * G5 - X * G4);
-    const double Xb = -G0b * beta * G1 + G1b * G0 + G2b * G1 + G3b * G2;
-    double betab = G0b * dG0 + G1b * dG1 + G2b * dG2 + G3b * dG3;
+    G1b = fma(rb, eta0, G1b);
+    G2b = fma(rb, mu, G2b);
+    // (d) G_n(beta, X): dG_n/dX = G_{n-1}, dG_0/dX = -beta G1, dG_n/dbeta = (n G_{n+2} - X G_{n+1})/2
+    const double hX = 0.5 * X;
+    const double dG0 = -hX * G1, dG1 = fma(-hX, G2, 0.5 * G3);
+    const double dG2 = fma(-hX, G3, G4), dG3 = fma(-hX, G4, 1.5 * G5);
+    const double Xb = fma(-G0b * beta, G1, fma(G1b, G0, fma(G2b, G1, G3b * G2)));
+    double betab = fma(G0b, dG0, fma(G1b, dG1, fma(G2b, dG2, G3b * dG3)));
     // (e) X implicit in F = r0 G1 + eta0 G2 + mu G3 - h = 0, dF/dX = r
     const double w = Xb * ri;
-    r0b -= w * G1;
-    eta0b -= w * G2;
-    mub -= w * G3;
-    betab -= w * (r0 * dG1 + eta0 * dG2 + mu * dG3);
+    r0b = fma(-w, G1, r0b);
+    eta0b = fma(-w, G2, eta0b);
+    mub = fma(-w, G3, mub);
+    betab = fma(-w, fma(r0, dG1, fma(eta0, dG2, mu * dG3)), betab);
     // (f) beta = 2 mu / r0 - v.v, eta0 = Q.v, r0 = |Q|
-    mub += 2.0 * betab * r0i;
-    r0b -= 2.0 * mu * betab * r0i * r0i;
-    nvx += -2.0 * betab * vx + eta0b * qx;
-    nvy += -2.0 * betab * vy + eta0b * qy;
-    nvz += -2.0 * betab * vz + eta0b * qz;
-    nqx += eta0b * vx + r0b * r0i * qx;
-    nqy += eta0b * vy + r0b * r0i * qy;
-    nqz += eta0b * vz + r0b * r0i * qz;
+    const double b2 = 2.0 * betab;
+    mub = fma(b2, r0i, mub);
+    r0b = fma(-b2 * A, r0i, r0b);
+    const double rq = r0b * r0i;
+    nvx = fma(-b2, vx, fma(eta0b, qx, nvx));
+    nvy = fma(-b2, vy, fma(eta0b, qy, nvy));
+    nvz = fma(-b2, vz, fma(eta0b, qz, nvz));
+    nqx = fma(eta0b, vx, fma(rq, qx, nqx));
+    nqy = fma(eta0b, vy, fma(rq, qy, nqy));
+    nqz = fma(eta0b, vz, fma(rq, qz, nqz));
     lqx = nqx; lqy = nqy; lqz = nqz;
     lvx = nvx; lvy = nvy; lvz = nvz;
     lmu += mub;
@@ -268,7 +283,8 @@ __device__ __forceinline__ void loss_body(const WhgState& st, const WhgBuckets& 
     const double wgt = (pl.has_sys && adj.weight) ? adj.weight[u] : 1.0;
     double lqx = 2.0 * wgt * ex, lqy = 2.0 * wgt * ey, lqz = 2.0 * wgt * ez;
     double lvx = 0.0, lvy = 0.0, lvz = 0.0, lmu = 0.0;
-    if (ns > 0) kepler_vjp<NT>(mu, 0.5 * dt, qx, qy, qz, vx, vy, vz, X, lqx, lqy, lqz, lvx, lvy, lvz, lmu);
+    if (ns > 0)
+        kepler_vjp<NT>(mu, 1.0 / mu, 0.5 * dt, qx, qy, qz, vx, vy, vz, X, lqx, lqy, lqz, lvx, lvy, lvz, lmu);
     if (!real) {
         lqx = lqy = lqz = lvx = lvy = lvz = lmu = 0.0;
     }
@@ -344,7 +360,7 @@ __device__ __forceinline__ void back_body(const WhgState& st, const WhgBuckets& 
     const double mu = pl.has_sys ? st.m0[s] : 1.0;
     const double dt = pl.has_sys ? st.dt[s] : 1.0e-3;
     const bool real = pl.has_sys && g.p < st.nplan[s];
-    const double hm = dt * m, c = (0.5 * dt) / mu;
+    const double hm = dt * m, c = (0.5 * dt) / mu, muinv = 1.0 / mu;
     const double kgr = GRM ? (-6.0 * mu * mu * dt) / (st.c_light * st.c_light) : 0.0;
     const double* tape = adj.tape + (size_t)buf * adj.tape_len;
     double* lam = adj.lam;
@@ -364,7 +380,7 @@ __device__ __forceinline__ void back_body(const WhgState& st, const WhgBuckets& 
         if (!merged) jump_vjp<L>(g, m, c, mu, v3x, v3y, v3z, lqx, lqy, lqz, lvx, lvy, lvz, lm, lmu);
         kick_vjp<L, GRM>(g, q2x, q2y, q2z, m, hm, dt, mu, kgr, lvx, lvy, lvz, lqx, lqy, lqz, lm, lmu);
         jump_vjp<L>(g, m, merged ? 2.0 * c : c, mu, v1x, v1y, v1z, lqx, lqy, lqz, lvx, lvy, lvz, lm, lmu);
-        kepler_vjp<NT>(mu, h, q0x, q0y, q0z, v0x, v0y, v0z, X, lqx, lqy, lqz, lvx, lvy, lvz, lmu);
+        kepler_vjp<NT>(mu, muinv, h, q0x, q0y, q0z, v0x, v0y, v0z, X, lqx, lqy, lqz, lvx, lvy, lvz, lmu);
         if (!real) {
             lqx = lqy = lqz = lvx = lvy = lvz = lm = lmu = 0.0;
         }
