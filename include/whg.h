@@ -118,6 +118,12 @@ typedef struct {
                                  memory (allocated by whg_create).  Not part of the
                                  paper's method.  Ignored by whg_integrate_noalloc.
                                  Default 0. */
+    int interaction_schedule; /* 0 (default): pairs at lane distance k < L/2 evaluated once
+                                 with the reaction passed back (Newton's third law, Sec. 3.3),
+                                 distance L/2 by both lanes: 4 reciprocal square roots per lane
+                                 for 8 planets.  1: all L-1 rotations, every lane summing its
+                                 own pairs (7 per lane for 8 planets).  Same map; the summation
+                                 order, and so the rounding, differs.  A tuning dimension. */
 } whg_options;
 
 /* Fill *opt with the defaults above. */

@@ -8,10 +8,11 @@ length) and keeps the fastest in a JSON cache:
   lane group for all systems (the power of two >= max planets),
 * CUDA block size (32, 64 or 128 threads),
 * steps per launch (automatic, or shorter launches),
-* CUDA-graph replay of step launches (off, or 16 launches per graph).
+* CUDA-graph replay of step launches (off, or 16 launches per graph),
+* interaction schedule (third-law rotations, or all L-1 rotations).
 
-Block size, launch length and graphs never change results; the packing only
-changes the order of the cross-lane sums (rounding).  The timing uses CUDA
+Block size, launch length and graphs never change results; the packing and
+the schedule only change the order of the sums (rounding).  The timing uses CUDA
 events around whg_step on the library's stream after a warm-up call of the
 same length.
 """
@@ -40,8 +41,9 @@ def candidates(ens):
     while uniform < nmax:
         uniform <<= 1
     lanes = [0] if uniform == nmax and np.all(ens.n_planets == nmax) else [0, uniform]
-    for L, block, spl, graph in itertools.product(lanes, (32, 64, 128), (0, 64), (0, 16)):
-        yield {"lanes_per_system": L, "block_size": block, "steps_per_launch": spl, "graph_launches": graph}
+    for L, block, spl, graph, sched in itertools.product(lanes, (32, 64, 128), (0, 64), (0, 16), (0, 1)):
+        yield {"lanes_per_system": L, "block_size": block, "steps_per_launch": spl, "graph_launches": graph,
+               "interaction_schedule": sched}
 
 
 def time_config(ens, cfg: dict, gr_mode: int, newton_terms: int, window_s: float = 0.05) -> float:
@@ -102,5 +104,6 @@ def tune(ens, gr_mode: int = 1, newton_terms: int = 8, cache_path: str | None = 
 def integrator(ens, gr_mode: int = 1, newton_terms: int = 8, **kw) -> "whg.Integrator":
     """An Integrator with the tuned launch configuration for this ensemble."""
     best = tune(ens, gr_mode, newton_terms, **kw)
-    cfg = {k: best[k] for k in ("lanes_per_system", "block_size", "steps_per_launch", "graph_launches")}
+    cfg = {k: best[k] for k in ("lanes_per_system", "block_size", "steps_per_launch", "graph_launches",
+                                "interaction_schedule")}
     return whg.Integrator(ens.n_systems, ens.max_planets, gr_mode=gr_mode, newton_terms=newton_terms, **cfg)

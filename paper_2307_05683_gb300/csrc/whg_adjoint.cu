@@ -335,7 +335,7 @@ __device__ __forceinline__ void tape_body(const WhgState& st, const WhgBuckets& 
         const bool merged = GRM == 0 && st.merge;
         jump<L>(g, m, merged ? 2.0 * c : c, vx, vy, vz, qx, qy, qz);
         tp[10 * NL] = qx; tp[11 * NL] = qy; tp[12 * NL] = qz;
-        kick<L, GRM>(g, qx, qy, qz, hm, mrat, kgr, nothr, vx, vy, vz);
+        kick<L, GRM>(g, qx, qy, qz, hm, mrat, kgr, nothr, vx, vy, vz, st.full_rotation != 0);
         tp[13 * NL] = vx; tp[14 * NL] = vy; tp[15 * NL] = vz;
         if (!merged) jump<L>(g, m, c, vx, vy, vz, qx, qy, qz);
         if (!real) {                                  // lanes without a planet stay parked

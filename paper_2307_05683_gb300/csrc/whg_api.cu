@@ -246,6 +246,7 @@ void whg_default_options(whg_options* opt)
     opt->merge_jumps = 0;
     opt->halley_fp32 = 0;
     opt->repack_frozen = 0;
+    opt->interaction_schedule = 0;
 }
 
 int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options* opt_in,
@@ -281,6 +282,8 @@ int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options*
         return fail(nullptr, WHG_EINVAL, "graph_launches=%d must be in 0..4096", opt.graph_launches);
     if (opt.repack_frozen != 0 && opt.repack_frozen != 1)
         return fail(nullptr, WHG_EINVAL, "repack_frozen=%d must be 0 or 1", opt.repack_frozen);
+    if (opt.interaction_schedule != 0 && opt.interaction_schedule != 1)
+        return fail(nullptr, WHG_EINVAL, "interaction_schedule=%d must be 0 or 1", opt.interaction_schedule);
 
     whg_ctx* c = new (std::nothrow) whg_ctx();
     if (!c) return fail(nullptr, WHG_ENOMEM, "host allocation failed");
@@ -330,6 +333,7 @@ int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options*
     st.eject = opt.eject_factor;
     st.merge = (opt.merge_jumps && opt.gr_mode == 0) ? 1 : 0;
     st.halley32 = opt.halley_fp32 ? 1 : 0;
+    st.full_rotation = opt.interaction_schedule == 1 ? 1 : 0;
 
     const size_t B = 1 + (size_t)max_planets;
     const size_t sd = (size_t)n_systems * (7 * B + 1);

@@ -432,47 +432,69 @@ __device__ __forceinline__ void jump(const Group<L>& g, double m, double jc, dou
 // pair at distance k (0 when the rule is off); returns true if a pair it
 // evaluates is closer (compared on the bit patterns of positive doubles, so
 // no FP64 instruction is spent).
+// `full` (uniform across the warp) selects the other schedule: all L-1
+// rotations, every lane summing its own pairs with no reactions (each pair
+// evaluated by both of its lanes: 7 reciprocal square roots per lane for
+// L = 8); the close-encounter test then uses the distances k <= L/2, which
+// cover every pair from one side.
 template <int L, int GRM>
 __device__ __forceinline__ bool kick(const Group<L>& g, double qx, double qy, double qz, double hm,
                                      double mrat, double kgr, const double* thr2, double& vx,
-                                     double& vy, double& vz)
+                                     double& vy, double& vz, bool full = false)
 {
     bool close = false;
+    if (full) {
 #pragma unroll
-    for (int k = 1; 2 * k < L; ++k) {
-        const int to = g.at(k), from = g.at(-k);
-        const double dx = __shfl_sync(WHG_FULL_MASK, qx, to) - qx;   // Q_j - Q_i
-        const double dy = __shfl_sync(WHG_FULL_MASK, qy, to) - qy;
-        const double dz = __shfl_sync(WHG_FULL_MASK, qz, to) - qz;
-        const double hmj = __shfl_sync(WHG_FULL_MASK, hm, to);
-        const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-        close |= __double_as_longlong(r2) < __double_as_longlong(thr2[k - 1]);
-        const double r3 = rsqrt_cubed(r2);
-        const double sj = hmj * r3;
-        vx = fma(sj, dx, vx);
-        vy = fma(sj, dy, vy);
-        vz = fma(sj, dz, vz);
-        const double si = hm * r3;                    // reaction on j: -si (Q_j - Q_i)
-        const double ex = __shfl_sync(WHG_FULL_MASK, dx, from);
-        const double ey = __shfl_sync(WHG_FULL_MASK, dy, from);
-        const double ez = __shfl_sync(WHG_FULL_MASK, dz, from);
-        const double es = __shfl_sync(WHG_FULL_MASK, si, from);
-        vx = fma(-es, ex, vx);
-        vy = fma(-es, ey, vy);
-        vz = fma(-es, ez, vz);
-    }
-    if (L >= 2 && (L & 1) == 0) {
-        const int to = g.at(L / 2);
-        const double dx = __shfl_sync(WHG_FULL_MASK, qx, to) - qx;
-        const double dy = __shfl_sync(WHG_FULL_MASK, qy, to) - qy;
-        const double dz = __shfl_sync(WHG_FULL_MASK, qz, to) - qz;
-        const double hmj = __shfl_sync(WHG_FULL_MASK, hm, to);
-        const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-        close |= __double_as_longlong(r2) < __double_as_longlong(thr2[L / 2 - 1]);
-        const double sj = hmj * rsqrt_cubed(r2);
-        vx = fma(sj, dx, vx);
-        vy = fma(sj, dy, vy);
-        vz = fma(sj, dz, vz);
+        for (int k = 1; k < L; ++k) {
+            const int to = g.at(k);
+            const double dx = __shfl_sync(WHG_FULL_MASK, qx, to) - qx;
+            const double dy = __shfl_sync(WHG_FULL_MASK, qy, to) - qy;
+            const double dz = __shfl_sync(WHG_FULL_MASK, qz, to) - qz;
+            const double hmj = __shfl_sync(WHG_FULL_MASK, hm, to);
+            const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+            if (2 * k <= L) close |= __double_as_longlong(r2) < __double_as_longlong(thr2[k - 1]);
+            const double sj = hmj * rsqrt_cubed(r2);
+            vx = fma(sj, dx, vx);
+            vy = fma(sj, dy, vy);
+            vz = fma(sj, dz, vz);
+        }
+    } else {
+#pragma unroll
+        for (int k = 1; 2 * k < L; ++k) {
+            const int to = g.at(k), from = g.at(-k);
+            const double dx = __shfl_sync(WHG_FULL_MASK, qx, to) - qx;   // Q_j - Q_i
+            const double dy = __shfl_sync(WHG_FULL_MASK, qy, to) - qy;
+            const double dz = __shfl_sync(WHG_FULL_MASK, qz, to) - qz;
+            const double hmj = __shfl_sync(WHG_FULL_MASK, hm, to);
+            const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+            close |= __double_as_longlong(r2) < __double_as_longlong(thr2[k - 1]);
+            const double r3 = rsqrt_cubed(r2);
+            const double sj = hmj * r3;
+            vx = fma(sj, dx, vx);
+            vy = fma(sj, dy, vy);
+            vz = fma(sj, dz, vz);
+            const double si = hm * r3;                    // reaction on j: -si (Q_j - Q_i)
+            const double ex = __shfl_sync(WHG_FULL_MASK, dx, from);
+            const double ey = __shfl_sync(WHG_FULL_MASK, dy, from);
+            const double ez = __shfl_sync(WHG_FULL_MASK, dz, from);
+            const double es = __shfl_sync(WHG_FULL_MASK, si, from);
+            vx = fma(-es, ex, vx);
+            vy = fma(-es, ey, vy);
+            vz = fma(-es, ez, vz);
+        }
+        if (L >= 2 && (L & 1) == 0) {
+            const int to = g.at(L / 2);
+            const double dx = __shfl_sync(WHG_FULL_MASK, qx, to) - qx;
+            const double dy = __shfl_sync(WHG_FULL_MASK, qy, to) - qy;
+            const double dz = __shfl_sync(WHG_FULL_MASK, qz, to) - qz;
+            const double hmj = __shfl_sync(WHG_FULL_MASK, hm, to);
+            const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+            close |= __double_as_longlong(r2) < __double_as_longlong(thr2[L / 2 - 1]);
+            const double sj = hmj * rsqrt_cubed(r2);
+            vx = fma(sj, dx, vx);
+            vy = fma(sj, dy, vy);
+            vz = fma(sj, dz, vz);
+        }
     }
     if (GRM != 0) {
         // a_GR(Q) = -6 (G m0)^2 Q / (c^2 |Q|^4); kgr = -6 m0^2 dt / c^2.
@@ -641,6 +663,7 @@ __device__ __forceinline__ void step_body(const WhgState& st, const WhgBuckets& 
     const double mrat = m / mu;
     const double kgr = GRM ? (-6.0 * mu * mu * dt) / (st.c_light * st.c_light) : 0.0;
     const bool h32 = st.halley32 != 0;
+    const bool full = st.full_rotation != 0;
     // close-encounter distances of this lane's pairs (once per launch)
     double thr2[4] = {0.0, 0.0, 0.0, 0.0};
     {
@@ -668,10 +691,10 @@ __device__ __forceinline__ void step_body(const WhgState& st, const WhgBuckets& 
         bool close;
         if (GRM == 0 && st.merge) {                   // J(dt) I(dt): J and I commute without GR
             jump<L>(g, m, 2.0 * jc, vx, vy, vz, qx, qy, qz);
-            close = kick<L, GRM>(g, qx, qy, qz, hm, mrat, kgr, thr2, vx, vy, vz);
+            close = kick<L, GRM>(g, qx, qy, qz, hm, mrat, kgr, thr2, vx, vy, vz, full);
         } else {
             jump<L>(g, m, jc, vx, vy, vz, qx, qy, qz);
-            close = kick<L, GRM>(g, qx, qy, qz, hm, mrat, kgr, thr2, vx, vy, vz);
+            close = kick<L, GRM>(g, qx, qy, qz, hm, mrat, kgr, thr2, vx, vy, vz, full);
             jump<L>(g, m, jc, vx, vy, vz, qx, qy, qz);
         }
         const bool fin = is_finite(qx) & is_finite(qy) & is_finite(qz) & is_finite(vx) &

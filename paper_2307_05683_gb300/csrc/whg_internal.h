@@ -35,6 +35,7 @@ struct WhgState {
     double eject;                    // ejection rule: factor on the largest initial a (0 = off)
     int merge;                       // one J(dt) before I(dt) (GR off only)
     int halley32;                    // Kepler solver: initial guess and Halley phase in FP32
+    int full_rotation;               // interaction: all L-1 rotations, no third-law reactions
 };
 
 // Bucket table (by value in every launch).

@@ -132,6 +132,7 @@ extern "C" int whg_integrate_noalloc(int n_systems, int max_planets, const whg_o
     st.eject = opt.eject_factor;
     st.merge = (opt.merge_jumps && opt.gr_mode == 0) ? 1 : 0;
     st.halley32 = opt.halley_fp32 ? 1 : 0;
+    st.full_rotation = opt.interaction_schedule == 1 ? 1 : 0;
 
     WhgBuckets bk{};
     bk.nb = 1;

@@ -38,7 +38,8 @@ class whg_options(ctypes.Structure):
                 ("block_size", ctypes.c_int), ("steps_per_launch", ctypes.c_longlong),
                 ("close_encounter_hill", ctypes.c_double), ("eject_factor", ctypes.c_double),
                 ("graph_launches", ctypes.c_int), ("merge_jumps", ctypes.c_int),
-                ("halley_fp32", ctypes.c_int), ("repack_frozen", ctypes.c_int)]
+                ("halley_fp32", ctypes.c_int), ("repack_frozen", ctypes.c_int),
+                ("interaction_schedule", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -297,7 +298,8 @@ class Integrator:
                  newton_terms: int = 8, lanes_per_system: int = 0, block_size: int = 0,
                  steps_per_launch: int = 0, close_encounter_hill: float = 0.0,
                  eject_factor: float = 0.0, graph_launches: int = 0, merge_jumps: bool = False,
-                 halley_fp32: bool = False, repack_frozen: bool = False, stream=None):
+                 halley_fp32: bool = False, repack_frozen: bool = False, interaction_schedule: int = 0,
+                 stream=None):
         opt = whg_default_options()
         opt.gr_mode = gr_mode
         if c_light is not None:
@@ -312,6 +314,7 @@ class Integrator:
         opt.merge_jumps = int(merge_jumps)
         opt.halley_fp32 = int(halley_fp32)
         opt.repack_frozen = int(repack_frozen)
+        opt.interaction_schedule = int(interaction_schedule)
         self.S, self.N = int(n_systems), int(max_planets)
         self.stream = stream if stream is not None else current_stream()
         self.ctx = whg_create(self.S, self.N, opt, self.stream)

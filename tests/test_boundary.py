@@ -59,10 +59,40 @@ def test_options_struct_layout(lib_path):
     assert o.c_light == pytest.approx(10065.32, rel=1e-5)
     assert o.close_encounter_hill == 0.0 and o.eject_factor == 0.0
     assert o.graph_launches == 0 and o.merge_jumps == 0 and o.halley_fp32 == 0
-    assert ctypes.sizeof(whg.whg_options) == 72
+    assert ctypes.sizeof(whg.whg_options) == 80
     # the library writes the last field: the C struct reaches as far as the ctypes one
     s = whg.whg_options()
     s.halley_fp32 = 12345
     s.repack_frozen = 6789
+    s.interaction_schedule = 4321
     whg.load().whg_default_options(ctypes.byref(s))
-    assert s.halley_fp32 == 0 and s.repack_frozen == 0
+    assert s.halley_fp32 == 0 and s.repack_frozen == 0 and s.interaction_schedule == 0
+
+
+@pytest.mark.parametrize("field,value", [("gr_mode", 3), ("newton_terms", 7), ("lanes_per_system", 9),
+                                         ("block_size", 48), ("steps_per_launch", -1),
+                                         ("graph_launches", 5000), ("repack_frozen", 2),
+                                         ("interaction_schedule", 2), ("close_encounter_hill", -1.0),
+                                         ("eject_factor", float("inf"))])
+def test_create_rejects_bad_options(lib_path, field, value):
+    """whg_create checks its options before any CUDA call: a bad value gives
+    WHG_EINVAL, no context, and a message naming the option."""
+    from paper_2307_05683_gb300 import whg
+    lib = whg.load()
+    o = whg.whg_default_options()
+    setattr(o, field, value)
+    h = ctypes.c_void_p(1)
+    rc = lib.whg_create(ctypes.byref(h), 16, 8, ctypes.byref(o), None)
+    assert rc == whg.WHG_EINVAL and not h.value
+    msg = lib.whg_last_error(None).decode()
+    key = {"close_encounter_hill": "stop rules", "eject_factor": "stop rules"}.get(field, field)
+    assert key in msg, msg
+
+
+def test_create_rejects_bad_sizes(lib_path):
+    from paper_2307_05683_gb300 import whg
+    lib = whg.load()
+    h = ctypes.c_void_p()
+    assert lib.whg_create(ctypes.byref(h), 0, 8, None, None) == whg.WHG_EINVAL
+    assert lib.whg_create(ctypes.byref(h), 4, 9, None, None) == whg.WHG_EINVAL
+    assert lib.whg_create(None, 4, 8, None, None) == whg.WHG_EINVAL

@@ -559,3 +559,23 @@ def test_uneven_batch_full_size_sampled(whg, orc):
     assert_parity(g, ref, 1e-10, sub.n_planets)
     assert set(np.unique(st)) <= {0, whg.WHG_STATUS_CLOSE_ENCOUNTER, whg.WHG_STATUS_EJECTED,
                                   whg.WHG_STATUS_CLOSE_ENCOUNTER | whg.WHG_STATUS_EJECTED}
+
+
+@pytest.mark.parametrize("case", ["solar_1", "solar_1e4", "compact", "stop_rules"])
+def test_full_rotation_schedule_matches_oracle(whg, orc, case):
+    """interaction_schedule = 1 (all L-1 rotations, no third-law reactions):
+    the same map as the oracle at the default path's tolerances, and the same
+    close-encounter stops."""
+    kw, okw = {}, {}
+    if case.startswith("solar"):
+        ens = inputs.solar_ensemble(2, 256)
+        n, tol = (1, 1e-12) if case == "solar_1" else (10000, 1e-9)
+    elif case == "compact":
+        ens, n, tol = inputs.compact_ensemble(5, 200), 500, 1e-10
+    else:
+        ens, n, tol = inputs.compact_ensemble(12, 300), 400, 1e-10
+        kw = dict(close_encounter_hill=6.0, eject_factor=3.0)
+        okw = dict(encounter_hill=6.0, eject_factor=3.0)
+    g = gpu_run(whg, ens, n, gr_mode=1, interaction_schedule=1, **kw)
+    o = oracle_run(orc, ens, n, gr_mode=1, **okw)
+    assert_parity(g, o, tol, ens.n_planets)
