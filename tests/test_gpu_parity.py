@@ -579,3 +579,37 @@ def test_full_rotation_schedule_matches_oracle(whg, orc, case):
     g = gpu_run(whg, ens, n, gr_mode=1, interaction_schedule=1, **kw)
     o = oracle_run(orc, ens, n, gr_mode=1, **okw)
     assert_parity(g, o, tol, ens.n_planets)
+
+
+def test_bench_workload_sampled():
+    """The benchmark's own workload and launch configuration: its 4096
+    Solar-System-shaped systems (bench.rank_workload, rank 0) advanced by one
+    1e4-step launch (the bench's chunk); 128 sampled systems against the
+    oracle to 1e-9, every system finite and running."""
+    import types
+    import bench
+    from paper_2307_05683_gb300 import build, whg
+    import oracle as orc_mod
+    build.build()
+    orc_mod.build()
+    args = types.SimpleNamespace(seed=2024, systems=4096)
+    ens = bench.rank_workload(args, 0)
+    it = whg.Integrator(4096, 8, gr_mode=1)
+    it.init(ens)
+    l0 = it.launches
+    it.step(10000)
+    assert it.launches - l0 == 1
+    pos, vel, st, t = it.read_state()
+    it.close()
+    assert np.all(st == 0) and np.all(np.isfinite(pos)) and np.all(np.isfinite(vel))
+    idx = np.sort(np.random.default_rng(11).choice(4096, 128, replace=False))
+    sub = ens.subset(idx)
+    o = orc_mod.OracleEnsemble(128, 8, gr_mode=1)
+    o.init(sub)
+    o.run_threads(10000, CORES)
+    po, vo, so, to = o.read_state()
+    assert np.array_equal(st[idx], so) and np.allclose(t[idx], to, rtol=1e-15, atol=0)
+    sx = np.abs(po).max(axis=(1, 2))[:, None, None]
+    su = np.abs(vo).max(axis=(1, 2))[:, None, None]
+    assert (np.abs(pos[idx] - po) / sx).max() <= 1e-9
+    assert (np.abs(vel[idx] - vo) / su).max() <= 1e-9
