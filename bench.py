@@ -76,7 +76,7 @@ def parse_args():
                    help="Kepler solver's initial guess and Halley steps in FP32 (1, an option) "
                         "or FP64 (0, the library default: every step in FP64)")
     p.add_argument("--block-size", type=int, default=0)
-    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU work of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seed", type=int, default=2024)
@@ -480,7 +480,7 @@ def run_whg(args):
     roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                 "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
                 "traffic": profiled_traffic(),
-                "kernel": "k_step<8,8,1> (FP64 pipe)",
+                "kernel": "k_step_queue<8,1> via queue_unit (FP64 pipe)",
                 "algorithmic_flops_per_system_step": flops,
                 "fp32_flops_per_system_step": START_FLOPS[(8, 8, args.gr_mode)] if args.halley_fp32 else 0,
                 "peak_basis": "recipe unit counts x clocks: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz",

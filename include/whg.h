@@ -124,6 +124,17 @@ typedef struct {
                                  for 8 planets.  1: all L-1 rotations, every lane summing its
                                  own pairs (7 per lane for 8 planets).  Same map; the summation
                                  order, and so the rounding, differs.  A tuning dimension. */
+    int queue_steps;          /* 1..10000 (default 100): a persistent work queue; resident
+                                 warps take (warp-group, queue_steps steps) units in order,
+                                 each waiting for its group's previous unit, so work moves
+                                 between SMs and no SM finishes late because it holds one warp
+                                 more than another (+3.5 % at 4096 8-planet systems, +7 % at
+                                 8192).  Queue launches use one-warp blocks (block_size does
+                                 not apply).  0: one warp per warp-group for the whole launch.
+                                 Results are bitwise the same either way.  A wait that exceeds
+                                 its limit (seconds; only possible after a fault) makes the
+                                 next whg_synchronize or whg_read_state return WHG_ECUDA.  Not
+                                 part of the paper's method. */
 } whg_options;
 
 /* Fill *opt with the defaults above. */

@@ -9,7 +9,8 @@ length) and keeps the fastest in a JSON cache:
 * CUDA block size (32, 64 or 128 threads),
 * steps per launch (automatic, or shorter launches),
 * CUDA-graph replay of step launches (off, or 16 launches per graph),
-* interaction schedule (third-law rotations, or all L-1 rotations).
+* interaction schedule (third-law rotations, or all L-1 rotations),
+* work queue (100-step units, or one warp per warp-group for a whole launch).
 
 Block size, launch length and graphs never change results; the packing and
 the schedule only change the order of the sums (rounding).  The timing uses CUDA
@@ -41,9 +42,12 @@ def candidates(ens):
     while uniform < nmax:
         uniform <<= 1
     lanes = [0] if uniform == nmax and np.all(ens.n_planets == nmax) else [0, uniform]
-    for L, block, spl, graph, sched in itertools.product(lanes, (32, 64, 128), (0, 64), (0, 16), (0, 1)):
+    for L, block, spl, graph, sched, queue in itertools.product(lanes, (32, 64, 128), (0, 64), (0, 16), (0, 1),
+                                                                (0, 100)):
+        if queue and block != 32:                    # queue launches always use one-warp blocks
+            continue
         yield {"lanes_per_system": L, "block_size": block, "steps_per_launch": spl, "graph_launches": graph,
-               "interaction_schedule": sched}
+               "interaction_schedule": sched, "queue_steps": queue}
 
 
 def time_config(ens, cfg: dict, gr_mode: int, newton_terms: int, window_s: float = 0.05) -> float:
@@ -105,5 +109,5 @@ def integrator(ens, gr_mode: int = 1, newton_terms: int = 8, **kw) -> "whg.Integ
     """An Integrator with the tuned launch configuration for this ensemble."""
     best = tune(ens, gr_mode, newton_terms, **kw)
     cfg = {k: best[k] for k in ("lanes_per_system", "block_size", "steps_per_launch", "graph_launches",
-                                "interaction_schedule")}
+                                "interaction_schedule", "queue_steps")}
     return whg.Integrator(ens.n_systems, ens.max_planets, gr_mode=gr_mode, newton_terms=newton_terms, **cfg)

@@ -50,6 +50,10 @@ struct whg_ctx {
     WhgState scratch;
     int* order;
     long long since_repack;   // step launches since the last repack
+    // work queue (opt.queue_steps > 0): unit counter, per-group chunks done, error flag
+    unsigned long long* q_next;
+    int* q_done;
+    int* q_err;
     char err[256];
 };
 
@@ -209,6 +213,31 @@ int* carve_state(WhgState& st, void* base, size_t L, size_t P)
     return ip;
 }
 
+// n_steps for every system on `stream`: one step kernel, or the work-queue
+// kernel (its counter and per-group flags cleared first).
+cudaError_t launch_steps(whg_ctx* c, long long n_steps, const WhgLaunch& l)
+{
+    if (!c->q_next)
+        return whg_launch_step(c->st, c->bk, n_steps, c->opt.newton_terms, c->opt.gr_mode, l);
+    const long long qs = c->opt.queue_steps;
+    WhgQueue q{c->q_next, c->q_done, c->q_err, qs, (int)((n_steps + qs - 1) / qs)};
+    cudaError_t e = cudaMemsetAsync(c->q_next, 0, sizeof(unsigned long long), l.stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(c->q_done, 0, sizeof(int) * (size_t)c->bk.warp0[c->bk.nb], l.stream);
+    if (e != cudaSuccess) return e;
+    return whg_launch_step_queue(c->st, c->bk, n_steps, c->opt.newton_terms, c->opt.gr_mode, q, l.stream);
+}
+
+// After a synchronization: a work-queue wait that gave up is an error.
+int check_queue(whg_ctx* c)
+{
+    if (!c->q_err) return WHG_OK;
+    int flag = 0;
+    WHG_CUDA(c, cudaMemcpy(&flag, c->q_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) return fail(c, WHG_ECUDA, "work-queue wait gave up (state of this context is inconsistent)");
+    return WHG_OK;
+}
+
 // Repack on `stream`: live systems first in every bucket, through the mirror
 // block, copied back so that every pointer (and captured graph) stays valid.
 cudaError_t enqueue_repack(whg_ctx* c, cudaStream_t stream)
@@ -247,6 +276,7 @@ void whg_default_options(whg_options* opt)
     opt->halley_fp32 = 0;
     opt->repack_frozen = 0;
     opt->interaction_schedule = 0;
+    opt->queue_steps = 100;
 }
 
 int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options* opt_in,
@@ -284,6 +314,8 @@ int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options*
         return fail(nullptr, WHG_EINVAL, "repack_frozen=%d must be 0 or 1", opt.repack_frozen);
     if (opt.interaction_schedule != 0 && opt.interaction_schedule != 1)
         return fail(nullptr, WHG_EINVAL, "interaction_schedule=%d must be 0 or 1", opt.interaction_schedule);
+    if (opt.queue_steps < 0 || opt.queue_steps > 10000)
+        return fail(nullptr, WHG_EINVAL, "queue_steps=%d must be in 0..10000", opt.queue_steps);
 
     whg_ctx* c = new (std::nothrow) whg_ctx();
     if (!c) return fail(nullptr, WHG_ENOMEM, "host allocation failed");
@@ -335,6 +367,22 @@ int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options*
     st.halley32 = opt.halley_fp32 ? 1 : 0;
     st.full_rotation = opt.interaction_schedule == 1 ? 1 : 0;
 
+    if (opt.queue_steps > 0) {                           // counter, per-group flags, error flag
+        const size_t qbytes = sizeof(unsigned long long) + sizeof(int) * ((size_t)c->warps_cap + 1);
+        void* qb = nullptr;
+        e = cudaMalloc(&qb, qbytes);
+        if (e == cudaSuccess) e = cudaMemset(qb, 0, qbytes);
+        if (e != cudaSuccess) {
+            if (qb) cudaFree(qb);
+            cudaFree(base);
+            if (c->repack_buf) cudaFree(c->repack_buf);
+            delete c;
+            return fail(nullptr, WHG_ENOMEM, "cudaMalloc(%zu): %s", qbytes, cudaGetErrorString(e));
+        }
+        c->q_next = (unsigned long long*)qb;
+        c->q_err = (int*)(c->q_next + 1);
+        c->q_done = c->q_err + 1;
+    }
     const size_t B = 1 + (size_t)max_planets;
     const size_t sd = (size_t)n_systems * (7 * B + 1);
     const size_t sbytes = sd * sizeof(double) + 2 * (size_t)n_systems * sizeof(int) +
@@ -344,6 +392,7 @@ int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options*
     if (e != cudaSuccess) {
         cudaFree(base);
         if (c->repack_buf) cudaFree(c->repack_buf);
+        if (c->q_next) cudaFree(c->q_next);
         delete c;
         return fail(nullptr, WHG_ENOMEM, "cudaMalloc(%zu): %s", sbytes, cudaGetErrorString(e));
     }
@@ -458,8 +507,7 @@ int whg_step(whg_ctx* c, long long n)
             cl.stream = c->capture;
             WHG_CUDA(c, cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal));
             cudaError_t e = cudaSuccess;
-            for (long long i = 0; i < G && e == cudaSuccess; ++i)
-                e = whg_launch_step(c->st, c->bk, chunk, c->opt.newton_terms, c->opt.gr_mode, cl);
+            for (long long i = 0; i < G && e == cudaSuccess; ++i) e = launch_steps(c, chunk, cl);
             if (e == cudaSuccess && c->repack_buf) e = enqueue_repack(c, c->capture);   // once per replay
             cudaGraph_t graph = nullptr;
             const cudaError_t e2 = cudaStreamEndCapture(c->capture, &graph);
@@ -483,8 +531,7 @@ int whg_step(whg_ctx* c, long long n)
     const long long every = G > 0 ? G : 16;              // step launches between repacks
     while (n > 0) {
         const long long k = n < chunk ? n : chunk;
-        int rc = launch_check(c, whg_launch_step(c->st, c->bk, k, c->opt.newton_terms, c->opt.gr_mode, l),
-                              "step kernel");
+        int rc = launch_check(c, launch_steps(c, k, l), "step kernel");
         if (rc) return rc;
         n -= k;
         if (c->repack_buf && ++c->since_repack >= every) {
@@ -526,7 +573,7 @@ int whg_read_state(whg_ctx* c, double* pos, double* vel, int* status, double* t)
         WHG_CUDA(c, cudaMemcpyAsync(status, dst, S * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     if (t) WHG_CUDA(c, cudaMemcpyAsync(t, dtm, S * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     WHG_CUDA(c, cudaStreamSynchronize(c->stream));
-    return WHG_OK;
+    return check_queue(c);
 }
 
 int whg_energy_device(whg_ctx* c, double* E)
@@ -606,7 +653,7 @@ int whg_synchronize(whg_ctx* c)
 {
     if (!c) return WHG_EINVAL;
     WHG_CUDA(c, cudaStreamSynchronize(c->stream));
-    return WHG_OK;
+    return check_queue(c);
 }
 
 long long whg_launch_count(const whg_ctx* c) { return c ? c->launches : 0; }
@@ -739,6 +786,7 @@ void whg_destroy(whg_ctx* c)
     cudaFree(c->st.m);
     cudaFree(c->stage_d);
     if (c->repack_buf) cudaFree(c->repack_buf);
+    if (c->q_next) cudaFree(c->q_next);
     if (c->adj_buf) cudaFree(c->adj_buf);
     if (c->side) {
         cudaStreamSynchronize(c->side);

@@ -639,7 +639,17 @@ __device__ __forceinline__ void init_body(const WhgState& st, const WhgBuckets& 
 }
 
 // n Wisdom-Holman steps, state in registers (Eq. 2 with fused drifts).
-template <int L, int NT, int GRM>
+// Load of state that other warps of the same launch may have written (the
+// work queue moves a warp-group between SMs): through L2, bypassing a
+// possibly stale L1 line.
+template <bool COH, typename T>
+__device__ __forceinline__ T ld_state(const T* p)
+{
+    if (COH) return __ldcg(p);
+    return *p;
+}
+
+template <int L, int NT, int GRM, bool COH = false>
 __device__ __forceinline__ void step_body(const WhgState& st, const WhgBuckets& bk, int b, int w,
                                           long long nsteps)
 {
@@ -648,13 +658,13 @@ __device__ __forceinline__ void step_body(const WhgState& st, const WhgBuckets& 
     const size_t lane = pl.lane;
     const int s = pl.sys;
     const double m = st.m[lane];
-    double qx = st.qx[lane], qy = st.qy[lane], qz = st.qz[lane];
-    double vx = st.vx[lane], vy = st.vy[lane], vz = st.vz[lane];
+    double qx = ld_state<COH>(st.qx + lane), qy = ld_state<COH>(st.qy + lane), qz = ld_state<COH>(st.qz + lane);
+    double vx = ld_state<COH>(st.vx + lane), vy = ld_state<COH>(st.vy + lane), vz = ld_state<COH>(st.vz + lane);
     const double mu = pl.has_sys ? st.m0[s] : 1.0;
     const double dt = pl.has_sys ? st.dt[s] : 1.0e-3;
     const int npl = pl.has_sys ? st.nplan[s] : 0;
-    int status = pl.has_sys ? st.status[s] : 0;
-    const long long nstep0 = pl.has_sys ? st.nstep[s] : 0;
+    int status = pl.has_sys ? ld_state<COH>(st.status + s) : 0;
+    const long long nstep0 = pl.has_sys ? ld_state<COH>(st.nstep + s) : 0;
     const double rej2 = pl.has_sys ? st.rej2[s] : 0.0;
     const bool real = pl.has_sys && g.p < npl;
     bool alive = pl.has_sys && status == 0;
@@ -888,6 +898,79 @@ __global__ void __launch_bounds__(WHG_MAX_BLOCK) k_step(WhgState st, WhgBuckets 
     if (w >= bk.warp0[bk.nb]) return;                // whole warps beyond the last bucket
     const int b = bucket_of(bk, w);
     WHG_DISPATCH_L(bk.L[b], (step_body<L_, NT, GRM>(st, bk, b, w, n)))
+}
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(int* p, int v)
+{
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Polls of a work-queue wait before giving up (each at least ~100 ns of
+// sleep: several seconds, against at most ~0.5 s for the longest legitimate
+// wait, one unit of 1e4 steps).
+constexpr long long kQueueSpinLimit = 1LL << 26;
+
+// Work queue over warp-groups (no counterpart in the paper).  Unit
+// u = k G + g advances warp-group g (one warp's worth of systems) by steps
+// [k chunk, min(n, (k+1) chunk)).  Resident warps take units in increasing u
+// from an atomic counter; unit (g, k) first waits until done[g] == k.  The
+// smallest incomplete u always has its predecessor complete and is held by
+// a running warp (a warp takes a unit only when it runs), so the queue
+// always progresses.  Work thus moves between SMs and the launch ends within
+// about one unit of the balanced time, whatever the warp count per SM.  A
+// wait that exceeds kQueueSpinLimit polls sets *err and ends the warp.
+// One unit of the work queue, kept out of line so that its step loop is
+// compiled as in k_step (the unit loop around it would otherwise keep the
+// bucket table in local memory).
+template <int L, int NT, int GRM>
+__device__ __noinline__ void queue_unit(const WhgState& st, const WhgBuckets& bk, int b, int g, long long m)
+{
+    step_body<L, NT, GRM, true>(st, bk, b, g, m);
+}
+
+template <int NT, int GRM>
+__global__ void __launch_bounds__(WHG_MAX_BLOCK) k_step_queue(WhgState st, WhgBuckets bk, long long n,
+                                                             WhgQueue q)
+{
+    const int G = bk.warp0[bk.nb];
+    const unsigned long long total = (unsigned long long)G * (unsigned long long)q.units;
+    const int lane = (int)(threadIdx.x & 31u);
+    for (;;) {
+        unsigned long long u = 0;
+        if (lane == 0) u = atomicAdd(q.next, 1ULL);
+        u = __shfl_sync(WHG_FULL_MASK, u, 0);
+        if (u >= total) return;
+        const int k = (int)(u / (unsigned long long)G), g = (int)(u % (unsigned long long)G);
+        int ok = 1;
+        if (lane == 0 && k > 0) {
+            long long polls = 0;
+            while (ld_acquire_gpu(q.done + g) < k) {
+                if (++polls > kQueueSpinLimit) {
+                    atomicExch(q.err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        ok = __shfl_sync(WHG_FULL_MASK, ok, 0);
+        if (!ok) return;
+        if (k > 0) (void)ld_acquire_gpu(q.done + g);  // every lane acquires before reading the state
+        const long long s0 = (long long)k * q.chunk;
+        const long long m = n - s0 < q.chunk ? n - s0 : q.chunk;
+        const int b = bucket_of(bk, g);
+        WHG_DISPATCH_L(bk.L[b], (queue_unit<L_, NT, GRM>(st, bk, b, g, m)))
+        __threadfence();                             // each lane's state stores, then the release
+        __syncwarp();
+        if (lane == 0) st_release_gpu(q.done + g, k + 1);
+    }
 }
 
 template <int NT>

@@ -38,6 +38,16 @@ struct WhgState {
     int full_rotation;               // interaction: all L-1 rotations, no third-law reactions
 };
 
+// Work-queue control of k_step_queue (device pointers; next and done zeroed
+// before each launch).
+struct WhgQueue {
+    unsigned long long* next;        // unit counter
+    int* done;                       // [warp-groups] chunks completed
+    int* err;                        // set to 1 when a wait gave up
+    long long chunk;                 // steps per unit
+    int units;                       // units per warp-group
+};
+
 // Bucket table (by value in every launch).
 struct WhgBuckets {
     int nb;                          // number of buckets, 1..8
@@ -100,12 +110,19 @@ cudaError_t whg_launch_repack(const WhgState& st, const WhgState& scratch, const
 cudaError_t whg_launch_raw(const WhgState&, const WhgBuckets&, const WhgOut&, int set, const WhgLaunch&);
 cudaError_t whg_launch_step(const WhgState&, const WhgBuckets&, long long nsteps, int newton_terms,
                             int gr_mode, const WhgLaunch&);
+// Step kernel over the work queue (q.next and q.done zeroed by the caller).
+cudaError_t whg_launch_step_queue(const WhgState&, const WhgBuckets&, long long nsteps, int newton_terms,
+                                  int gr_mode, const WhgQueue& q, cudaStream_t stream);
 cudaError_t whg_launch_read(const WhgState&, const WhgBuckets&, const WhgOut&, int newton_terms,
                             const WhgLaunch&);
 cudaError_t whg_launch_energy(const WhgState&, const WhgBuckets&, const WhgOut&, int newton_terms,
                               int gr_mode, const WhgLaunch&);
 cudaError_t whg_launch_step_nt6(const WhgState&, const WhgBuckets&, long long, int, const WhgLaunch&);
 cudaError_t whg_launch_step_nt8(const WhgState&, const WhgBuckets&, long long, int, const WhgLaunch&);
+cudaError_t whg_launch_step_queue_nt6(const WhgState&, const WhgBuckets&, long long, int, const WhgQueue&,
+                                      cudaStream_t);
+cudaError_t whg_launch_step_queue_nt8(const WhgState&, const WhgBuckets&, long long, int, const WhgQueue&,
+                                      cudaStream_t);
 cudaError_t whg_launch_read_nt6(const WhgState&, const WhgBuckets&, const WhgOut&, const WhgLaunch&);
 cudaError_t whg_launch_read_nt8(const WhgState&, const WhgBuckets&, const WhgOut&, const WhgLaunch&);
 cudaError_t whg_launch_energy_nt6(const WhgState&, const WhgBuckets&, const WhgOut&, int, const WhgLaunch&);

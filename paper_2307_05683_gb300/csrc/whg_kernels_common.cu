@@ -159,6 +159,13 @@ cudaError_t whg_launch_step(const WhgState& st, const WhgBuckets& bk, long long 
                              : whg_launch_step_nt8(st, bk, n, gr_mode, l);
 }
 
+cudaError_t whg_launch_step_queue(const WhgState& st, const WhgBuckets& bk, long long n, int newton_terms,
+                                  int gr_mode, const WhgQueue& q, cudaStream_t stream)
+{
+    return newton_terms == 6 ? whg_launch_step_queue_nt6(st, bk, n, gr_mode, q, stream)
+                             : whg_launch_step_queue_nt8(st, bk, n, gr_mode, q, stream);
+}
+
 cudaError_t whg_launch_read(const WhgState& st, const WhgBuckets& bk, const WhgOut& o, int newton_terms,
                             const WhgLaunch& l)
 {

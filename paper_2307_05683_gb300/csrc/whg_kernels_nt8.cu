@@ -14,6 +14,36 @@ cudaError_t whg_launch_step_nt8(const WhgState& st, const WhgBuckets& bk, long l
     return cudaGetLastError();
 }
 
+namespace {
+
+// One warp per block; as many blocks as can be resident at once (capped at
+// the number of warp-groups), so every warp of the launch runs from the start.
+template <typename Kernel>
+cudaError_t launch_queue(Kernel kern, const WhgState& st, const WhgBuckets& bk, long long n,
+                         const WhgQueue& q, cudaStream_t stream)
+{
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, 0);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    long long grid = (long long)(per_sm > 0 ? per_sm : 1) * sms;
+    if (grid > bk.warp0[bk.nb]) grid = bk.warp0[bk.nb];
+    if (grid < 1) return cudaSuccess;
+    kern<<<(int)grid, 32, 0, stream>>>(st, bk, n, q);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t whg_launch_step_queue_nt8(const WhgState& st, const WhgBuckets& bk, long long n, int gr_mode,
+                                       const WhgQueue& q, cudaStream_t stream)
+{
+    if (gr_mode == 0) return launch_queue(whg::k_step_queue<8, 0>, st, bk, n, q, stream);
+    if (gr_mode == 1) return launch_queue(whg::k_step_queue<8, 1>, st, bk, n, q, stream);
+    return launch_queue(whg::k_step_queue<8, 2>, st, bk, n, q, stream);
+}
+
 cudaError_t whg_launch_read_nt8(const WhgState& st, const WhgBuckets& bk, const WhgOut& o,
                                   const WhgLaunch& l)
 {

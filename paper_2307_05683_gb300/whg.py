@@ -39,7 +39,7 @@ class whg_options(ctypes.Structure):
                 ("close_encounter_hill", ctypes.c_double), ("eject_factor", ctypes.c_double),
                 ("graph_launches", ctypes.c_int), ("merge_jumps", ctypes.c_int),
                 ("halley_fp32", ctypes.c_int), ("repack_frozen", ctypes.c_int),
-                ("interaction_schedule", ctypes.c_int)]
+                ("interaction_schedule", ctypes.c_int), ("queue_steps", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -299,7 +299,7 @@ class Integrator:
                  steps_per_launch: int = 0, close_encounter_hill: float = 0.0,
                  eject_factor: float = 0.0, graph_launches: int = 0, merge_jumps: bool = False,
                  halley_fp32: bool = False, repack_frozen: bool = False, interaction_schedule: int = 0,
-                 stream=None):
+                 queue_steps: int = 100, stream=None):
         opt = whg_default_options()
         opt.gr_mode = gr_mode
         if c_light is not None:
@@ -315,6 +315,7 @@ class Integrator:
         opt.halley_fp32 = int(halley_fp32)
         opt.repack_frozen = int(repack_frozen)
         opt.interaction_schedule = int(interaction_schedule)
+        opt.queue_steps = int(queue_steps)
         self.S, self.N = int(n_systems), int(max_planets)
         self.stream = stream if stream is not None else current_stream()
         self.ctx = whg_create(self.S, self.N, opt, self.stream)

@@ -111,3 +111,34 @@ def test_repacking_stopped_systems_is_bitwise_neutral(whg, graphs):
     assert np.array_equal(ref.energy(), E, equal_nan=True)
     ref.close()
     assert rep[-1] > plain[-1]                        # the repack kernels are counted
+
+
+@pytest.mark.parametrize("extra", [{}, {"graph_launches": 4, "steps_per_launch": 250},
+                                   {"repack_frozen": True, "steps_per_launch": 250}])
+def test_work_queue_is_bitwise_identical(whg, extra):
+    """queue_steps moves warp-groups between SMs in units of steps; each
+    system's arithmetic is unchanged, so every output matches the default
+    path bit for bit (mixed planet counts, stop rules, graphs, repacking)."""
+    ens = inputs.compact_ensemble(46, 900)
+    kw = dict(close_encounter_hill=8.0, eject_factor=3.0, **extra)
+    plain = _run(whg, ens, 1500, queue_steps=0, **kw)
+    queued = _run(whg, ens, 1500, queue_steps=37, **kw)
+    assert int((plain[2] != 0).sum()) > 50
+    for a, b in zip(plain[:-1], queued[:-1]):
+        assert np.array_equal(a, b)
+
+
+def test_work_queue_bench_size_is_bitwise_identical(whg):
+    """4096 Solar-System-shaped systems (1024 warp-groups over 152 SMs),
+    3000 steps in 100-step units against one plain launch."""
+    ens = inputs.solar_ensemble(47, 4096)
+    plain = _run(whg, ens, 3000, queue_steps=0)
+    queued = _run(whg, ens, 3000, queue_steps=100)
+    for a, b in zip(plain[:-1], queued[:-1]):
+        assert np.array_equal(a, b)
+    it = whg.Integrator(64, 8, queue_steps=10)
+    it.init(inputs.solar_ensemble(48, 64))
+    it.step(0)
+    it.step(5)                                       # fewer steps than one unit
+    it.synchronize()
+    it.close()
