@@ -129,8 +129,10 @@ typedef struct {
                                  each waiting for its group's previous unit, so work moves
                                  between SMs and no SM finishes late because it holds one warp
                                  more than another (+3.5 % at 4096 8-planet systems, +7 % at
-                                 8192).  Queue launches use one-warp blocks (block_size does
-                                 not apply).  0: one warp per warp-group for the whole launch.
+                                 8192).  Used for launches of at least 4 units per warp-group
+                                 (shorter ones run as plain launches); queue launches use
+                                 one-warp blocks (block_size does not apply).  0: one warp per
+                                 warp-group for the whole launch.
                                  Results are bitwise the same either way.  A wait that exceeds
                                  its limit (seconds; only possible after a fault) makes the
                                  next whg_synchronize or whg_read_state return WHG_ECUDA.  Not

@@ -213,13 +213,18 @@ int* carve_state(WhgState& st, void* base, size_t L, size_t P)
     return ip;
 }
 
-// n_steps for every system on `stream`: one step kernel, or the work-queue
-// kernel (its counter and per-group flags cleared first).
+// n_steps for every system on `stream`: the work-queue kernel (its counter
+// and per-group flags cleared first) when the launch spans at least
+// kQueueMinUnits units per warp-group, else one step kernel.  With fewer
+// units there is nothing to rebalance (measured: one unit per group costs
+// ~5 % on 65,536 compact systems).
+constexpr long long kQueueMinUnits = 4;
+
 cudaError_t launch_steps(whg_ctx* c, long long n_steps, const WhgLaunch& l)
 {
-    if (!c->q_next)
-        return whg_launch_step(c->st, c->bk, n_steps, c->opt.newton_terms, c->opt.gr_mode, l);
     const long long qs = c->opt.queue_steps;
+    if (!c->q_next || n_steps < kQueueMinUnits * qs)
+        return whg_launch_step(c->st, c->bk, n_steps, c->opt.newton_terms, c->opt.gr_mode, l);
     WhgQueue q{c->q_next, c->q_done, c->q_err, qs, (int)((n_steps + qs - 1) / qs)};
     cudaError_t e = cudaMemsetAsync(c->q_next, 0, sizeof(unsigned long long), l.stream);
     if (e == cudaSuccess)

@@ -136,9 +136,15 @@ def test_work_queue_bench_size_is_bitwise_identical(whg):
     queued = _run(whg, ens, 3000, queue_steps=100)
     for a, b in zip(plain[:-1], queued[:-1]):
         assert np.array_equal(a, b)
+    small = inputs.solar_ensemble(48, 64)
     it = whg.Integrator(64, 8, queue_steps=10)
-    it.init(inputs.solar_ensemble(48, 64))
+    it.init(small)
     it.step(0)
-    it.step(5)                                       # fewer steps than one unit
+    it.step(5)                                       # below 4 units: a plain launch
+    it.step(45)                                      # 5 units, the last one partial
     it.synchronize()
+    got = it.read_state()
     it.close()
+    ref = _run(whg, small, 50, queue_steps=0)
+    for a, b in zip(got, ref[:4]):
+        assert np.array_equal(a, b)
