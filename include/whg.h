@@ -306,11 +306,14 @@ int whg_kepler_sweep(const double* q, const double* v, const int* cfg, int n, do
 int whg_probe_fp64_lanes(int warps_per_sm, int active_lanes, int iters, float* ms);
 
 /* The library's own reciprocal, reciprocal square root and FP64 <-> FP32
- * conversions next to CUDA's, for testing: out [6][n] DEVICE buffer receives
- * rcp_own(x), 1/x (CUDA, IEEE), rsqrt_own(x), rsqrt(x) (CUDA) (x > 0 for the
- * square roots, else 0), the own FP64 -> FP32 -> FP64 round trip of x, and
- * CUDA's round-toward-zero FP64 -> FP32 conversion of x widened to FP64, for
- * the n DEVICE inputs x.  Blocks. */
+ * conversions next to CUDA's, for testing: out [10][n] DEVICE buffer receives
+ * rcp_own(x), 1/x (CUDA, IEEE), rsqrt_own(x), rsqrt(x) (CUDA) (0 < x < 4e307
+ * for the square roots, else 0), the own FP64 -> FP32 -> FP64 round trip of
+ * x, CUDA's round-toward-zero FP64 -> FP32 conversion of x widened to FP64,
+ * then the own routines' FP64-only reference forms: rcp, rsqrt, the own
+ * x^(-3/2) and its reference (0 <= x < 4e307, else 0), for the n DEVICE
+ * inputs x.
+ * Blocks. */
 int whg_test_special(const double* x, int n, double* out);
 
 #ifdef __cplusplus

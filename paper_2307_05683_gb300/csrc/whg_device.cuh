@@ -57,7 +57,53 @@ __device__ __forceinline__ float approx_rsqrt_f32(float x)
     return r;
 }
 
-// 1/x for finite normal x (either sign).
+// ------------------------------------------------------------------------
+// Integer-pipe pieces of the reciprocal and reciprocal square root.  On this
+// GPU an FP64 warp instruction holds the FP64 pipe for 64 cycles and an
+// integer one its pipe for about 1, so exact integer forms replace FP64
+// operations wherever the operands are short: the seeds y below carry 24
+// significant bits (an FP32 approximation widened to FP64).
+
+// D 2^-s rounded to the nearest double (ties to even); D a signed 64-bit
+// integer, the result a normal double or zero.
+__device__ __forceinline__ double scaled_int_to_double(long long D, int s)
+{
+    const unsigned long long sign = D < 0 ? 0x8000000000000000ULL : 0ULL;
+    const unsigned long long a = D < 0 ? 0ULL - (unsigned long long)D : (unsigned long long)D;
+    const int lz = __clzll((long long)a);
+    const unsigned long long n = a << (lz & 63);             // leading one at bit 63
+    unsigned long long m = n >> 11;                          // 53 bits
+    const unsigned long long rem = n & 0x7ffULL;
+    m += (rem > 0x400ULL || (rem == 0x400ULL && (m & 1ULL))) ? 1ULL : 0ULL;
+    const unsigned long long carry = m >> 53;                // rounding reached 2^53
+    m >>= carry;
+    const long long E = 63 - lz - s + 1023 + (long long)carry;
+    const unsigned long long bits = sign | ((unsigned long long)E << 52) | (m & 0x000fffffffffffffULL);
+    return a ? __longlong_as_double((long long)bits) : 0.0;
+}
+
+// The double with biased exponent E and fraction bits f, saturated as the
+// FP64 product would be: +inf above the exponent range (a zero or tiny
+// argument of the reciprocal square roots), 0 below it.
+__device__ __forceinline__ double exp_bits_to_double(long long E, unsigned long long f)
+{
+    const unsigned long long bits = E >= 0x7ff ? 0x7ff0000000000000ULL
+                                  : (E <= 0 ? 0ULL : (((unsigned long long)E << 52) | f));
+    return __longlong_as_double((long long)bits);
+}
+
+// 53-bit significand of a finite normal double as an integer.
+__device__ __forceinline__ unsigned long long significand(unsigned hi, unsigned lo)
+{
+    return ((unsigned long long)((hi & 0x000fffffu) | 0x00100000u) << 32) | lo;
+}
+
+// 1/x for finite x with 2^-1022 <= |x| < 2^1021 (either sign; 1/x normal):
+// FP32 seed y (24 bits), then
+// y (1 + e + e^2) with e = 1 - x y.  The seed is within ~2^-22 of 1/x, so
+// x y = 2^s - D with |D| < 2^55 and s = 202 - (y's FP32 exponent) >= 64:
+// D = -(Mx My mod 2^64) in wrap-around integer arithmetic, and e = D 2^-s
+// rounded once, the value fma(-x, y, 1) gives.  2 FP64 operations.
 __device__ __forceinline__ double rcp(double x)
 {
     const unsigned hi = (unsigned)__double2hiint(x);
@@ -65,15 +111,29 @@ __device__ __forceinline__ double rcp(double x)
     const int ex = (int)((hi >> 20) & 0x7ffu);                         // biased exponent
     const float mant = __uint_as_float(0x3f800000u | ((hi & 0x000fffffu) << 3) | (lo >> 29));
     const unsigned rb = __float_as_uint(approx_rcp_f32(mant));          // in (0.5, 1]
-    const int dex = (int)((rb >> 23) & 0xffu) - 127 + 2046 - ex;        // biased exponent of 1/x
+    const int erb = (int)((rb >> 23) & 0xffu);
+    const int dex = erb - 127 + 2046 - ex;                              // biased exponent of 1/x
     const unsigned yhi = (hi & 0x80000000u) | ((unsigned)dex << 20) | ((rb >> 3) & 0x000fffffu);
     const double y = __hiloint2double((int)yhi, (int)(rb << 29));
-    const double e = fma(-x, y, 1.0);
+    const unsigned long long My = (rb & 0x007fffffu) | 0x00800000u;
+    const long long D = (long long)(0ULL - significand(hi, lo) * My);
+    double e = scaled_int_to_double(D, 202 - erb);
+    // outside the domain keep the IEEE outcome of the FP64 form: zero and
+    // subnormal x give an infinite result, inf and NaN a NaN
+    e = ex == 0 ? __longlong_as_double(0x7ff0000000000000LL) : e;
+    e = ex == 0x7ff ? __longlong_as_double(0x7ff8000000000000LL) : e;
     return fma(y, fma(e, e, e), y);
 }
 
-// 1/sqrt(x) for finite normal x > 0.
-__device__ __forceinline__ double rsqrt(double x)
+// Seed of x^(-1/2) for finite normal 0 < x < 2^1022: y (24-bit significand
+// My, biased exponent dex), y^2 exactly (48 bits) and y^3 rounded to nearest,
+// all on the integer pipe.
+struct RsqrtSeed {
+    double y, y2, y3;
+};
+
+template <bool CUBE>
+__device__ __forceinline__ RsqrtSeed rsqrt_seed(double x)
 {
     const unsigned hi = (unsigned)__double2hiint(x);
     const unsigned lo = (unsigned)__double2loint(x);
@@ -84,32 +144,48 @@ __device__ __forceinline__ double rsqrt(double x)
                                        (lo >> 29));                    // in [1, 4)
     const unsigned rb = __float_as_uint(approx_rsqrt_f32(mant));       // in (0.5, 1]
     const int dex = (int)((rb >> 23) & 0xffu) - 127 - half + 1023;
-    const double y = __hiloint2double((int)(((unsigned)dex << 20) | ((rb >> 3) & 0x000fffffu)),
-                                      (int)(rb << 29));
-    const double e = fma(-x, y * y, 1.0);
-    return fma(y * e, fma(0.375, e, 0.5), y);
+    RsqrtSeed r;
+    r.y = __hiloint2double((int)(((unsigned)dex << 20) | ((rb >> 3) & 0x000fffffu)), (int)(rb << 29));
+    const unsigned long long My = (rb & 0x007fffffu) | 0x00800000u;
+    const unsigned long long S = My * My;                              // [2^46, 2^48), exact
+    const unsigned long long top = S >> 47;
+    const unsigned long long f2 = (S << (6 - top)) & 0x000fffffffffffffULL;
+    r.y2 = exp_bits_to_double(2 * dex - 1023 + (long long)top, f2);
+    r.y3 = 0.0;
+    if (CUBE) {                                                        // My^3 in [2^69, 2^72)
+        const unsigned long long clo = S * My, chi = __umul64hi(S, My);
+        const int p = 127 - __clzll((long long)chi);                   // leading-one position
+        const int sh = p - 52;                                         // 17..19
+        unsigned long long m = ((clo >> sh) | (chi << (64 - sh))) & 0x001fffffffffffffULL;
+        const unsigned long long rem = clo & ((1ULL << sh) - 1ULL), hb = 1ULL << (sh - 1);
+        m += (rem > hb || (rem == hb && (m & 1ULL))) ? 1ULL : 0ULL;
+        const unsigned long long carry = m >> 53;
+        m >>= carry;
+        const long long E = p + 3 * dex - 2115 + (long long)carry;
+        r.y3 = exp_bits_to_double(E, m & 0x000fffffffffffffULL);
+    }
+    return r;
 }
 
-// x^(-3/2) for finite normal x > 0 (the 1/r^3 of a pair from r^2), straight
-// from the rsqrt seed: x^(-3/2) = y0^3 (1 - e)^(-3/2) = y0^3 (1 + 3e/2 + 15e^2/8 + ...)
-// with e = 1 - x y0^2; truncation ~ (35/16) e^3 < 2^-61.
+// 1/sqrt(x) for finite normal 0 < x < 2^1022: y (1 + e/2 + 3e^2/8),
+// e = 1 - x y^2.  4 FP64 operations.
+__device__ __forceinline__ double rsqrt(double x)
+{
+    const RsqrtSeed r = rsqrt_seed<false>(x);
+    const double e = fma(-x, r.y2, 1.0);
+    return fma(r.y * e, fma(0.375, e, 0.5), r.y);
+}
+
+// x^(-3/2) for 2^-681 < x < 2^682 (the result a normal double; the 1/r^3
+// of a pair from r^2),
+// straight from the rsqrt seed: x^(-3/2) = y^3 (1 - e)^(-3/2) = y^3 (1 +
+// 3e/2 + 15e^2/8 + ...) with e = 1 - x y^2; truncation ~ (35/16) e^3 < 2^-61.
+// 4 FP64 operations.
 __device__ __forceinline__ double rsqrt_cubed(double x)
 {
-    const unsigned hi = (unsigned)__double2hiint(x);
-    const unsigned lo = (unsigned)__double2loint(x);
-    const int ex = (int)((hi >> 20) & 0x7ffu) - 1023;
-    const int odd = ex & 1;
-    const int half = (ex - odd) / 2;
-    const float mant = __uint_as_float(((unsigned)(127 + odd) << 23) | ((hi & 0x000fffffu) << 3) |
-                                       (lo >> 29));
-    const unsigned rb = __float_as_uint(approx_rsqrt_f32(mant));
-    const int dex = (int)((rb >> 23) & 0xffu) - 127 - half + 1023;
-    const double y = __hiloint2double((int)(((unsigned)dex << 20) | ((rb >> 3) & 0x000fffffu)),
-                                      (int)(rb << 29));
-    const double y2 = y * y;
-    const double e = fma(-x, y2, 1.0);
-    const double y3 = y2 * y;
-    return fma(y3 * e, fma(1.875, e, 1.5), y3);
+    const RsqrtSeed r = rsqrt_seed<true>(x);
+    const double e = fma(-x, r.y2, 1.0);
+    return fma(r.y3 * e, fma(1.875, e, 1.5), r.y3);
 }
 
 // FP64 -> FP32 from the bit fields (sign, exponent rebiased from 1023 to

@@ -110,17 +110,69 @@ __global__ void k_kepler_sweep(const double* q, const double* v, const int* cfg,
     vo[3 * i] = vx; vo[3 * i + 1] = vy; vo[3 * i + 2] = vz;
 }
 
+// The same seeds refined with FP64 operations only (e = fma(-x, y, 1),
+// y^2 = y*y, y^3 = y^2*y): the references the integer-pipe forms in
+// whg_device.cuh must reproduce bit for bit.
+__device__ double rcp_fp64_ref(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    const int ex = (int)((hi >> 20) & 0x7ffu);
+    const float mant = __uint_as_float(0x3f800000u | ((hi & 0x000fffffu) << 3) | (lo >> 29));
+    const unsigned rb = __float_as_uint(whg::approx_rcp_f32(mant));
+    const int dex = (int)((rb >> 23) & 0xffu) - 127 + 2046 - ex;
+    const unsigned yhi = (hi & 0x80000000u) | ((unsigned)dex << 20) | ((rb >> 3) & 0x000fffffu);
+    const double y = __hiloint2double((int)yhi, (int)(rb << 29));
+    const double e = fma(-x, y, 1.0);
+    return fma(y, fma(e, e, e), y);
+}
+
+__device__ double rsqrt_seed_ref(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    const int ex = (int)((hi >> 20) & 0x7ffu) - 1023;
+    const int odd = ex & 1;
+    const int half = (ex - odd) / 2;
+    const float mant = __uint_as_float(((unsigned)(127 + odd) << 23) | ((hi & 0x000fffffu) << 3) | (lo >> 29));
+    const unsigned rb = __float_as_uint(whg::approx_rsqrt_f32(mant));
+    const int dex = (int)((rb >> 23) & 0xffu) - 127 - half + 1023;
+    return __hiloint2double((int)(((unsigned)dex << 20) | ((rb >> 3) & 0x000fffffu)), (int)(rb << 29));
+}
+
+__device__ double rsqrt_fp64_ref(double x)
+{
+    const double y = rsqrt_seed_ref(x);
+    const double e = fma(-x, y * y, 1.0);
+    return fma(y * e, fma(0.375, e, 0.5), y);
+}
+
+__device__ double rsqrt_cubed_fp64_ref(double x)
+{
+    const double y = rsqrt_seed_ref(x);
+    const double y2 = y * y;
+    const double e = fma(-x, y2, 1.0);
+    const double y3 = y2 * y;
+    return fma(y3 * e, fma(1.875, e, 1.5), y3);
+}
+
 __global__ void k_special(const double* x, int n, double* out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double v = x[i];
+    const bool pos = v > 0.0 && v < 4.0e307;          // the rsqrt routines' domain (below 2^1022)
     out[i] = whg::rcp(v);
     out[n + i] = 1.0 / v;
-    out[2 * n + i] = v > 0.0 ? whg::rsqrt(v) : 0.0;
-    out[3 * n + i] = v > 0.0 ? ::rsqrt(v) : 0.0;
+    out[2 * n + i] = pos ? whg::rsqrt(v) : 0.0;
+    out[3 * n + i] = pos ? ::rsqrt(v) : 0.0;
     out[4 * n + i] = whg::to_f64(whg::to_f32(v));
     out[5 * n + i] = (double)__double2float_rz(v);
+    out[6 * n + i] = rcp_fp64_ref(v);
+    out[7 * n + i] = pos ? rsqrt_fp64_ref(v) : 0.0;
+    const bool nonneg = v >= 0.0 && v < 4.0e307;      // also zero: a coincident pair's r^2
+    out[8 * n + i] = nonneg ? whg::rsqrt_cubed(v) : 0.0;
+    out[9 * n + i] = nonneg ? rsqrt_cubed_fp64_ref(v) : 0.0;
 }
 
 }  // namespace

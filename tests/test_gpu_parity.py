@@ -81,9 +81,9 @@ def test_own_rcp_rsqrt_against_cuda(whg):
                         10.0 ** rng.uniform(-6, 6, 200000),
                         1.0 + rng.uniform(-1e-9, 1e-9, 1000), [1.0, 2.0, 4.0, 0.5, 3.0]])
     xt = torch.tensor(x, dtype=torch.float64, device="cuda")
-    out = torch.empty(6 * x.size, dtype=torch.float64, device="cuda")
+    out = torch.empty(10 * x.size, dtype=torch.float64, device="cuda")
     whg.whg_test_special(xt, out)
-    r = out.cpu().numpy().reshape(6, -1)
+    r = out.cpu().numpy().reshape(10, -1)
     ulp_rcp = np.spacing(np.abs(r[1]))
     ulp_rsq = np.spacing(np.abs(r[3]))
     # CUDA's 1/x is correctly rounded; rsqrt is within 1 ulp of exact.
@@ -96,6 +96,47 @@ def test_own_rcp_rsqrt_against_cuda(whg):
     exact_rsq = 1 / np.sqrt(xl)
     err = np.abs(r[2][sel].astype(np.longdouble) - exact_rsq) / np.spacing(np.abs(r[3][sel]))
     assert float(err.max()) <= 1.5
+
+
+def test_integer_pipe_refinement_matches_fp64_forms(whg):
+    """The reciprocal forms e = 1 - x y exactly on the integer pipe, and
+    x^(-1/2) and x^(-3/2) build y^2 and y^3 there: bit for bit the values of
+    the same refinements written with FP64 operations (fma(-x, y, 1), y*y,
+    y^2*y), over each routine's domain (1/x normal; x^(-3/2) normal) and
+    both signs for 1/x."""
+    import torch
+    rng = np.random.default_rng(4)
+    mag = 10.0 ** rng.uniform(-307, 307, 400000)
+    x = np.concatenate([mag, -mag[:100000], np.ldexp(1.0, np.arange(-1021, 1023)),
+                        np.nextafter(np.ldexp(1.0, np.arange(-1021, 1023)), np.inf),
+                        1.0 + rng.uniform(-1e-7, 1e-7, 20000)])
+    xt = torch.tensor(x, dtype=torch.float64, device="cuda")
+    out = torch.empty(10 * x.size, dtype=torch.float64, device="cuda")
+    whg.whg_test_special(xt, out)
+    r = out.cpu().numpy().reshape(10, -1)
+    inv = np.abs(x) < 2.0 ** 1021                            # 1/x normal
+    assert inv.sum() > 500000 and np.array_equal(r[0][inv], r[6][inv])      # rcp
+    pos = (x > 0) & (x < 4.0e307)
+    assert np.array_equal(r[2][pos], r[7][pos])              # rsqrt
+    cube = (x > 2.0 ** -680) & (x < 2.0 ** 681)               # x^(-3/2) normal
+    assert np.array_equal(r[8][cube], r[9][cube])            # x^(-3/2)
+    sel = pos & (x > 1e-200) & (x < 1e200)
+    exact = np.asarray(x[sel], np.longdouble) ** np.longdouble(-1.5)
+    err = np.abs(r[8][sel].astype(np.longdouble) - exact) / np.spacing(np.abs(r[8][sel]))
+    assert float(err.max()) <= 2.0
+    # outside the domains the outcomes stay non-finite as in the FP64 forms: a
+    # zero or subnormal argument gives the same infinite 1/x and x^(-3/2) (a
+    # coincident pair of planets then freezes its system as non-finite), inf
+    # and NaN give NaN (the FP64 form gives some non-finite value)
+    sp = np.array([0.0, -0.0, 5e-324, -1e-310, np.inf, -np.inf, np.nan])
+    spt = torch.tensor(sp, dtype=torch.float64, device="cuda")
+    o = torch.empty(10 * sp.size, dtype=torch.float64, device="cuda")
+    whg.whg_test_special(spt, o)
+    q = o.cpu().numpy().reshape(10, -1)
+    assert np.all(np.isinf(q[0][:4])) and np.array_equal(np.signbit(q[0][:4]), np.signbit(sp[:4]))
+    assert np.all(np.isnan(q[0][4:]))
+    assert np.array_equal(q[0][:4], q[6][:4]) and not np.any(np.isfinite(q[6][4:]))
+    assert np.all(np.isinf(q[8][:3])) and np.array_equal(q[8][:3], q[9][:3])    # x^(-3/2) of 0, -0, 5e-324
 
 
 def test_own_fp32_conversions_against_cuda(whg):
@@ -112,9 +153,9 @@ def test_own_fp32_conversions_against_cuda(whg):
                         [0.0, -0.0, 1e-300, -1e-300, 1e300, -1e300, np.inf, -np.inf, np.nan,
                          float(np.finfo(np.float32).max), float(np.finfo(np.float32).tiny)]])
     xt = torch.tensor(x, dtype=torch.float64, device="cuda")
-    out = torch.empty(6 * x.size, dtype=torch.float64, device="cuda")
+    out = torch.empty(10 * x.size, dtype=torch.float64, device="cuda")
     whg.whg_test_special(xt, out)
-    r = out.cpu().numpy().reshape(6, -1)
+    r = out.cpu().numpy().reshape(10, -1)
     own, rz = r[4], r[5]
     ax = np.abs(x)
     normal = np.isfinite(x) & (ax >= 2.0 ** -126) & (ax < 2.0 ** 128)
