@@ -305,6 +305,15 @@ int whg_kepler_sweep(const double* q, const double* v, const int* cfg, int n, do
  * lanes cost full FP64 pipe time. */
 int whg_probe_fp64_lanes(int warps_per_sm, int active_lanes, int iters, float* ms);
 
+/* Failure-path test of the work queue (no counterpart in the paper): one
+ * queue launch on ctx (initialized, queue_steps > 0) whose unit counter starts
+ * past every warp-group's first unit, so each unit waits for a predecessor
+ * that never runs.  Every wait gives up after spin_limit polls (>= 1; ~100 ns
+ * or more each) and sets the queue's error flag; no step runs, so the state
+ * is untouched.  *flag receives the flag (1 = a wait gave up), which is then
+ * cleared.  Blocks.  Returns WHG_EINVAL if the queue is off. */
+int whg_test_queue_timeout(whg_ctx* ctx, long long spin_limit, int* flag);
+
 /* The library's own reciprocal, reciprocal square root and FP64 <-> FP32
  * conversions next to CUDA's, for testing: out [10][n] DEVICE buffer receives
  * rcp_own(x), 1/x (CUDA, IEEE), rsqrt_own(x), rsqrt(x) (CUDA) (0 < x < 4e307

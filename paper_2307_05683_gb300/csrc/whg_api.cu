@@ -220,12 +220,17 @@ int* carve_state(WhgState& st, void* base, size_t L, size_t P)
 // ~5 % on 65,536 compact systems).
 constexpr long long kQueueMinUnits = 4;
 
+// Polls of a work-queue wait before it gives up (each at least ~100 ns of
+// sleep: several seconds, against at most ~0.5 s for the longest legitimate
+// wait, one unit of 1e4 steps).
+constexpr long long kQueueSpinLimit = 1LL << 26;
+
 cudaError_t launch_steps(whg_ctx* c, long long n_steps, const WhgLaunch& l)
 {
     const long long qs = c->opt.queue_steps;
     if (!c->q_next || n_steps < kQueueMinUnits * qs)
         return whg_launch_step(c->st, c->bk, n_steps, c->opt.newton_terms, c->opt.gr_mode, l);
-    WhgQueue q{c->q_next, c->q_done, c->q_err, qs, (int)((n_steps + qs - 1) / qs)};
+    WhgQueue q{c->q_next, c->q_done, c->q_err, qs, (int)((n_steps + qs - 1) / qs), kQueueSpinLimit};
     cudaError_t e = cudaMemsetAsync(c->q_next, 0, sizeof(unsigned long long), l.stream);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(c->q_done, 0, sizeof(int) * (size_t)c->bk.warp0[c->bk.nb], l.stream);
@@ -239,7 +244,10 @@ int check_queue(whg_ctx* c)
     if (!c->q_err) return WHG_OK;
     int flag = 0;
     WHG_CUDA(c, cudaMemcpy(&flag, c->q_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (flag) return fail(c, WHG_ECUDA, "work-queue wait gave up (state of this context is inconsistent)");
+    if (flag) {
+        WHG_CUDA(c, cudaMemset(c->q_err, 0, sizeof(int)));   // reported once
+        return fail(c, WHG_ECUDA, "work-queue wait gave up (state of this context is inconsistent)");
+    }
     return WHG_OK;
 }
 
@@ -662,6 +670,25 @@ int whg_synchronize(whg_ctx* c)
 }
 
 long long whg_launch_count(const whg_ctx* c) { return c ? c->launches : 0; }
+
+int whg_test_queue_timeout(whg_ctx* c, long long spin_limit, int* flag)
+{
+    if (!c || !flag || spin_limit < 1) return WHG_EINVAL;
+    if (!c->q_next) return fail(c, WHG_EINVAL, "the work queue is off (queue_steps = 0)");
+    if (!c->initialized) return fail(c, WHG_ESTATE, "whg_test_queue_timeout before whg_init");
+    const unsigned long long G = (unsigned long long)c->bk.warp0[c->bk.nb];
+    const long long qs = c->opt.queue_steps;
+    // the counter starts past every group's first unit, whose completion
+    // each remaining unit then waits for in vain
+    WhgQueue q{c->q_next, c->q_done, c->q_err, qs, 2, spin_limit};
+    WHG_CUDA(c, cudaMemcpyAsync(c->q_next, &G, sizeof G, cudaMemcpyHostToDevice, c->stream));
+    WHG_CUDA(c, cudaMemsetAsync(c->q_done, 0, sizeof(int) * (size_t)G, c->stream));
+    WHG_CUDA(c, whg_launch_step_queue(c->st, c->bk, 2 * qs, c->opt.newton_terms, c->opt.gr_mode, q, c->stream));
+    WHG_CUDA(c, cudaStreamSynchronize(c->stream));
+    WHG_CUDA(c, cudaMemcpy(flag, c->q_err, sizeof(int), cudaMemcpyDeviceToHost));
+    WHG_CUDA(c, cudaMemset(c->q_err, 0, sizeof(int)));
+    return WHG_OK;
+}
 
 const char* whg_last_error(const whg_ctx* c) { return c ? c->err : g_create_err; }
 

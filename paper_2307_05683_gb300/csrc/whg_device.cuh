@@ -988,10 +988,6 @@ __device__ __forceinline__ void st_release_gpu(int* p, int v)
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Polls of a work-queue wait before giving up (each at least ~100 ns of
-// sleep: several seconds, against at most ~0.5 s for the longest legitimate
-// wait, one unit of 1e4 steps).
-constexpr long long kQueueSpinLimit = 1LL << 26;
 
 // Work queue over warp-groups (no counterpart in the paper).  Unit
 // u = k G + g advances warp-group g (one warp's worth of systems) by steps
@@ -1001,7 +997,7 @@ constexpr long long kQueueSpinLimit = 1LL << 26;
 // a running warp (a warp takes a unit only when it runs), so the queue
 // always progresses.  Work thus moves between SMs and the launch ends within
 // about one unit of the balanced time, whatever the warp count per SM.  A
-// wait that exceeds kQueueSpinLimit polls sets *err and ends the warp.
+// wait that exceeds q.spin_limit polls sets *err and ends the warp.
 // One unit of the work queue, kept out of line so that its step loop is
 // compiled as in k_step (the unit loop around it would otherwise keep the
 // bucket table in local memory).
@@ -1028,7 +1024,7 @@ __global__ void __launch_bounds__(WHG_MAX_BLOCK) k_step_queue(WhgState st, WhgBu
         if (lane == 0 && k > 0) {
             long long polls = 0;
             while (ld_acquire_gpu(q.done + g) < k) {
-                if (++polls > kQueueSpinLimit) {
+                if (++polls > q.spin_limit) {
                     atomicExch(q.err, 1);
                     ok = 0;
                     break;

@@ -46,6 +46,7 @@ struct WhgQueue {
     int* err;                        // set to 1 when a wait gave up
     long long chunk;                 // steps per unit
     int units;                       // units per warp-group
+    long long spin_limit;            // polls before a wait gives up
 };
 
 // Bucket table (by value in every launch).

@@ -80,6 +80,7 @@ def load():
             "whg_test_special": (ctypes.c_int, [D, ctypes.c_int, D]),
             "whg_probe_fp64_lanes": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                     ctypes.POINTER(ctypes.c_float)]),
+            "whg_test_queue_timeout": (ctypes.c_int, [P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)]),
             "whg_kepler_sweep": (ctypes.c_int, [D, D, I, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                                 ctypes.c_longlong, D, D]),
             "whg_adjoint_forward": (ctypes.c_int, [P, ctypes.c_longlong, ctypes.c_int, D, D]),
@@ -103,7 +104,7 @@ def exported_symbols() -> list[str]:
             "whg_energy_device", "whg_get_raw", "whg_set_raw", "whg_synchronize",
             "whg_launch_count", "whg_last_error", "whg_destroy", "whg_measure_fp64_tflops",
             "whg_test_special", "whg_integrate_noalloc", "whg_adjoint_forward",
-            "whg_adjoint_backward", "whg_kepler_sweep", "whg_probe_fp64_lanes"]
+            "whg_adjoint_backward", "whg_kepler_sweep", "whg_probe_fp64_lanes", "whg_test_queue_timeout"]
 
 
 def _check(ctx, rc: int) -> None:
@@ -265,6 +266,13 @@ def whg_probe_fp64_lanes(warps_per_sm: int, active_lanes: int, iters: int) -> fl
     _check(None, load().whg_probe_fp64_lanes(int(warps_per_sm), int(active_lanes), int(iters),
                                              ctypes.byref(ms)))
     return float(ms.value)
+
+
+def whg_test_queue_timeout(ctx, spin_limit: int) -> int:
+    """Error flag (1 = a wait gave up) of the queue failure-path test (see whg.h)."""
+    flag = ctypes.c_int()
+    _check(ctx, load().whg_test_queue_timeout(ctx, int(spin_limit), ctypes.byref(flag)))
+    return int(flag.value)
 
 
 def whg_test_special(x, out) -> None:

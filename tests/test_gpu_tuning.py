@@ -148,3 +148,27 @@ def test_work_queue_bench_size_is_bitwise_identical(whg):
     ref = _run(whg, small, 50, queue_steps=0)
     for a, b in zip(got, ref[:4]):
         assert np.array_equal(a, b)
+
+
+def test_work_queue_wait_gives_up_and_context_stays_usable(whg):
+    """Failure path of the work queue without a fault: every unit waits for
+    a predecessor that never runs; each wait gives up after a few thousand
+    polls, sets the error flag that the host reads, and leaves the state and
+    the context usable (the next steps equal those of a fresh context)."""
+    ens = inputs.solar_ensemble(49, 256)
+    it = whg.Integrator(256, 8, queue_steps=50)
+    it.init(ens)
+    assert whg.whg_test_queue_timeout(it.ctx, 1 << 12) == 1
+    it.synchronize()                                 # the flag was reported and cleared
+    it.step(400)                                     # 8 units: a queue launch
+    it.synchronize()
+    got = it.read_state()
+    it.close()
+    ref = _run(whg, ens, 400, queue_steps=0)
+    for a, b in zip(got, ref[:4]):
+        assert np.array_equal(a, b)
+    off = whg.Integrator(8, 8, queue_steps=0)
+    off.init(inputs.solar_ensemble(50, 8))
+    with pytest.raises(whg.WhgError):
+        whg.whg_test_queue_timeout(off.ctx, 10)
+    off.close()
