@@ -127,14 +127,23 @@ def job_throughput(world: int, systems: int, chunk: int, steps: int, max_ms: flo
     return world * systems * chunk * steps / (max_ms / 1e3)
 
 
+def code_only(text: str) -> str:
+    """C/CUDA source without comments and with whitespace runs collapsed (the
+    code a compiler sees; string literals in these files hold no comment
+    markers)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_hash() -> str:
-    """Hash of the sources that define the step kernel (device code and its
-    instantiation with 8-term Newton-phase series)."""
+    """Hash of the code that defines the step kernel (device code and its
+    instantiation with 8-term Newton-phase series), comments excluded."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2307_05683_gb300", "csrc")
     for name in ("whg_device.cuh", "whg_kernels_nt8.cu"):
         h.update(name.encode())
-        h.update(open(os.path.join(csrc, name), "rb").read())
+        h.update(code_only(open(os.path.join(csrc, name)).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -10,14 +10,18 @@
 // spends integer and FP32 work freely to save FP64 instructions:
 //   * reciprocals and reciprocal square roots start from the FP32 hardware
 //     approximation of a mantissa built with integer operations and take one
-//     third-order FP64 refinement (3 and 5 FP64 instructions);
+//     third-order FP64 refinement whose exact pieces (1 - x y, y^2, y^3) are
+//     formed on the integer pipe (1/x: 2, x^(-1/2) and x^(-3/2): 4 FP64
+//     instructions);
 //   * the all-pairs interaction uses Newton's third law (Sec. 3.3), with
 //     partner schedules that suit warp shuffles rather than AVX512 lanes;
-//   * cross-lane sums are xor butterflies over the system's lanes (Sec. 3.4)
-//     when L is a power of two, else a gather in fixed lane order; either way
-//     every lane gets the bitwise-identical total.
-// State stays in registers for the whole launch; HBM is touched only at load
-// and store (coalesced: consecutive lanes read consecutive doubles).
+//   * cross-lane sums of 3-vectors are reduce-scatters by xor partners when L
+//     is 4 or 8 (Sec. 3.4 reduces with a butterfly), else gathers in fixed
+//     lane order; either way every lane gets the bitwise-identical total;
+//   * a persistent work queue moves (warp-group, steps) units between SMs so
+//     that no SM finishes late.
+// State stays in registers during a unit of steps; HBM is touched only at
+// load and store (coalesced: consecutive lanes read consecutive doubles).
 #pragma once
 
 #include <stdint.h>

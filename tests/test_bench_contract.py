@@ -62,3 +62,11 @@ def test_reference_arm_prints_the_contract_line(orc):
     assert cb["per_core"] > 0 and isinstance(cb["cpu_model"], str) and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_kernel_hash_ignores_comments_only():
+    bench = importlib.import_module("bench")
+    a = "int f(int x) { // doubles x\n  return 2 * x; /* plain */ }"
+    b = "int f(int x) {\n  return 2 * x;\n}  // other words"
+    c = "int f(int x) { return 3 * x; }"
+    assert bench.code_only(a) == bench.code_only(b) != bench.code_only(c)
