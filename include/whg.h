@@ -314,6 +314,16 @@ int whg_probe_fp64_lanes(int warps_per_sm, int active_lanes, int iters, float* m
  * cleared.  Blocks.  Returns WHG_EINVAL if the queue is off. */
 int whg_test_queue_timeout(whg_ctx* ctx, long long spin_limit, int* flag);
 
+/* Index checks (no counterpart in the paper; the stand-in for a device memory
+ * checker): in the debug build of the library (libwhg_debug.so, compiled with
+ * WHG_DEBUG_BOUNDS) every kernel checks its lane, system, bucket, permutation,
+ * repack and work-queue indices against the context's sizes and records a
+ * failed check as a bit in a flag word (1 lane, 2 system, 4 caller index,
+ * 8 bucket, 16 repack order, 32 queue unit) instead of trapping.  Synchronizes
+ * ctx's stream, writes the bits set since the last call to *flag and clears
+ * them.  In the release build: *flag = 0 and WHG_EINVAL. */
+int whg_debug_bounds(whg_ctx* ctx, unsigned* flag);
+
 /* The library's own reciprocal, reciprocal square root and FP64 <-> FP32
  * conversions next to CUDA's, for testing: out [10][n] DEVICE buffer receives
  * rcp_own(x), 1/x (CUDA, IEEE), rsqrt_own(x), rsqrt(x) (CUDA) (0 < x < 4e307

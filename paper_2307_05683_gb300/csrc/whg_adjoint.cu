@@ -255,7 +255,7 @@ template <int L, int NT>
 __device__ __forceinline__ void loss_body(const WhgState& st, const WhgBuckets& bk, const WhgAdj& adj,
                                           int b, int w, int start)
 {
-    const Place<L> pl(bk, b, w);
+    const Place<L> pl(st, bk, b, w);
     const Group<L>& g = pl.g;
     const size_t lane = pl.lane;
     const int s = pl.sys;
@@ -306,7 +306,7 @@ template <int L, int NT, int GRM>
 __device__ __forceinline__ void tape_body(const WhgState& st, const WhgBuckets& bk, const WhgAdj& adj,
                                           int b, int w, int seg, long long s0, int nk, int buf)
 {
-    const Place<L> pl(bk, b, w);
+    const Place<L> pl(st, bk, b, w);
     const Group<L>& g = pl.g;
     const size_t lane = pl.lane;
     const int s = pl.sys;
@@ -351,7 +351,7 @@ template <int L, int NT, int GRM>
 __device__ __forceinline__ void back_body(const WhgState& st, const WhgBuckets& bk, const WhgAdj& adj,
                                           int b, int w, long long s0, int nk, int buf)
 {
-    const Place<L> pl(bk, b, w);
+    const Place<L> pl(st, bk, b, w);
     const Group<L>& g = pl.g;
     const size_t lane = pl.lane;
     const int s = pl.sys;
@@ -396,7 +396,7 @@ template <int L>
 __device__ __forceinline__ void finish_body(const WhgState& st, const WhgBuckets& bk, const WhgAdj& adj,
                                             int b, int w)
 {
-    const Place<L> pl(bk, b, w);
+    const Place<L> pl(st, bk, b, w);
     const Group<L>& g = pl.g;
     const size_t lane = pl.lane;
     const size_t NL = adj.NL;

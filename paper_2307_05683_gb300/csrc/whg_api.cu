@@ -359,6 +359,16 @@ int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options*
     WhgState& st = c->st;
     c->perm_d = carve_state(st, base, L, P);
     st.perm = nullptr;
+    st.nl = (long long)L;
+#ifdef WHG_DEBUG_BOUNDS
+    e = cudaMalloc(&st.dbg, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(st.dbg, 0, sizeof(unsigned));
+    if (e != cudaSuccess) {
+        cudaFree(base);
+        delete c;
+        return fail(nullptr, WHG_ENOMEM, "cudaMalloc(bounds flag): %s", cudaGetErrorString(e));
+    }
+#endif
     if (opt.repack_frozen) {                             // mirror block + order array
         e = cudaMalloc(&c->repack_buf, bytes + P * sizeof(int));
         if (e != cudaSuccess) {
@@ -369,6 +379,8 @@ int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options*
         }
         c->scratch.perm = carve_state(c->scratch, c->repack_buf, L, P);
         c->scratch.S = n_systems;
+        c->scratch.nl = (long long)L;
+        c->scratch.dbg = st.dbg;
         c->order = (int*)((char*)c->repack_buf + bytes);
     }
     st.S = n_systems;
@@ -671,6 +683,20 @@ int whg_synchronize(whg_ctx* c)
 
 long long whg_launch_count(const whg_ctx* c) { return c ? c->launches : 0; }
 
+int whg_debug_bounds(whg_ctx* c, unsigned* flag)
+{
+    if (!c || !flag) return WHG_EINVAL;
+#ifdef WHG_DEBUG_BOUNDS
+    WHG_CUDA(c, cudaStreamSynchronize(c->stream));
+    WHG_CUDA(c, cudaMemcpy(flag, c->st.dbg, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    WHG_CUDA(c, cudaMemset(c->st.dbg, 0, sizeof(unsigned)));
+    return WHG_OK;
+#else
+    *flag = 0;
+    return fail(c, WHG_EINVAL, "index checks are not compiled in (build with debug=True)");
+#endif
+}
+
 int whg_test_queue_timeout(whg_ctx* c, long long spin_limit, int* flag)
 {
     if (!c || !flag || spin_limit < 1) return WHG_EINVAL;
@@ -819,6 +845,7 @@ void whg_destroy(whg_ctx* c)
     cudaFree(c->stage_d);
     if (c->repack_buf) cudaFree(c->repack_buf);
     if (c->q_next) cudaFree(c->q_next);
+    if (c->st.dbg) cudaFree(c->st.dbg);
     if (c->adj_buf) cudaFree(c->adj_buf);
     if (c->side) {
         cudaStreamSynchronize(c->side);

@@ -606,18 +606,24 @@ struct Place {
     int sys;             // internal system index (valid only if has_sys)
     bool has_sys;
     size_t lane;         // index into the lane arrays
-    __device__ __forceinline__ Place(const WhgBuckets& bk, int b, int w)
+    __device__ __forceinline__ Place(const WhgState& st, const WhgBuckets& bk, int b, int w)
     {
         const int sl = (w - bk.warp0[b]) * Group<L>::SPW + g.slot;
         has_sys = g.in_group && sl < bk.sys0[b + 1] - bk.sys0[b];
         sys = has_sys ? bk.sys0[b] + sl : 0;
         lane = (size_t)w * 32 + g.lane;
+        WHG_CHECK(st, b >= 0 && b < bk.nb, WHG_BOUND_BUCKET);
+        WHG_CHECK(st, (long long)lane < st.nl, WHG_BOUND_LANE);
+        WHG_CHECK(st, !has_sys || (sys >= 0 && sys < st.S), WHG_BOUND_SYSTEM);
+        (void)st;
     }
 };
 
 __device__ __forceinline__ int user_index(const WhgState& st, int sys)
 {
-    return st.perm ? st.perm[sys] : sys;
+    const int u = st.perm ? st.perm[sys] : sys;
+    WHG_CHECK(st, sys >= 0 && sys < st.S && u >= 0 && u < st.S, WHG_BOUND_USER);
+    return u;
 }
 
 // ------------------------------------------------------------------------
@@ -630,7 +636,7 @@ template <int L>
 __device__ __forceinline__ void init_body(const WhgState& st, const WhgBuckets& bk, const WhgIn& in,
                                           int b, int w)
 {
-    const Place<L> pl(bk, b, w);
+    const Place<L> pl(st, bk, b, w);
     const int p = pl.g.p;
     const size_t lane = pl.lane;
     int n = 0, ok = 0;
@@ -733,7 +739,7 @@ template <int L, int NT, int GRM, bool COH = false>
 __device__ __forceinline__ void step_body(const WhgState& st, const WhgBuckets& bk, int b, int w,
                                           long long nsteps)
 {
-    const Place<L> pl(bk, b, w);
+    const Place<L> pl(st, bk, b, w);
     const Group<L>& g = pl.g;
     const size_t lane = pl.lane;
     const int s = pl.sys;
@@ -822,7 +828,7 @@ template <int L, int NT>
 __device__ __forceinline__ void read_body(const WhgState& st, const WhgBuckets& bk, const WhgOut& out,
                                           int b, int w)
 {
-    const Place<L> pl(bk, b, w);
+    const Place<L> pl(st, bk, b, w);
     const Group<L>& g = pl.g;
     const size_t lane = pl.lane;
     const int s = pl.sys;
@@ -873,7 +879,7 @@ template <int L, int NT, int GRM>
 __device__ __forceinline__ void energy_body(const WhgState& st, const WhgBuckets& bk,
                                             const WhgOut& out, int b, int w)
 {
-    const Place<L> pl(bk, b, w);
+    const Place<L> pl(st, bk, b, w);
     const Group<L>& g = pl.g;
     const size_t lane = pl.lane;
     const int s = pl.sys;
@@ -913,7 +919,7 @@ template <int L>
 __device__ __forceinline__ void raw_body(const WhgState& st, const WhgBuckets& bk, const WhgOut& io,
                                          int set, int b, int w)
 {
-    const Place<L> pl(bk, b, w);
+    const Place<L> pl(st, bk, b, w);
     if (!pl.has_sys) return;                         // no shuffles in this body
     const size_t lane = pl.lane;
     const int s = pl.sys, p = pl.g.p;
@@ -1024,6 +1030,7 @@ __global__ void __launch_bounds__(WHG_MAX_BLOCK) k_step_queue(WhgState st, WhgBu
         u = __shfl_sync(WHG_FULL_MASK, u, 0);
         if (u >= total) return;
         const int k = (int)(u / (unsigned long long)G), g = (int)(u % (unsigned long long)G);
+        WHG_CHECK(st, g >= 0 && g < G && k < q.units, WHG_BOUND_QUEUE);
         int ok = 1;
         if (lane == 0 && k > 0) {
             long long polls = 0;

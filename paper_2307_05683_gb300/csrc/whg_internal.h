@@ -36,7 +36,27 @@ struct WhgState {
     int merge;                       // one J(dt) before I(dt) (GR off only)
     int halley32;                    // Kepler solver: initial guess and Halley phase in FP32
     int full_rotation;               // interaction: all L-1 rotations, no third-law reactions
+    long long nl;                    // lane capacity of the lane arrays
+    unsigned* dbg;                   // bounds-check flag word (debug builds only, else null)
 };
+
+// Index checks of the debug build (-DWHG_DEBUG_BOUNDS; the stand-in for a
+// memory checker): a failed check sets a bit of *st.dbg, never traps.  The
+// release build compiles them away.
+#define WHG_BOUND_LANE 1u          // lane index outside the lane arrays
+#define WHG_BOUND_SYSTEM 2u        // internal system index outside 0..S-1
+#define WHG_BOUND_USER 4u          // caller's system index (perm) outside 0..S-1
+#define WHG_BOUND_BUCKET 8u        // bucket index outside 0..nb-1
+#define WHG_BOUND_REPACK 16u       // repack order outside the bucket
+#define WHG_BOUND_QUEUE 32u        // work-queue unit outside the warp-groups
+#ifdef WHG_DEBUG_BOUNDS
+#define WHG_CHECK(st, cond, bit)                                  \
+    do {                                                          \
+        if (!(cond)) atomicOr((st).dbg, (bit));                   \
+    } while (0)
+#else
+#define WHG_CHECK(st, cond, bit) ((void)0)
+#endif
 
 // Work-queue control of k_step_queue (device pointers; next and done zeroed
 // before each launch).

@@ -96,9 +96,11 @@ __global__ void __launch_bounds__(256) k_repack_gather(WhgState src, WhgState ds
     if (slot < spw && local < bk.sys0[b + 1] - bk.sys0[b]) {
         s_new = bk.sys0[b] + local;
         s_old = order[s_new];
+        WHG_CHECK(src, s_old >= bk.sys0[b] && s_old < bk.sys0[b + 1], WHG_BOUND_REPACK);
         const int lo = s_old - bk.sys0[b];
         from = (size_t)(bk.warp0[b] + lo / spw) * 32 + (size_t)(lo % spw) * L + p;
     }
+    WHG_CHECK(src, (long long)from < src.nl && li < src.nl, WHG_BOUND_LANE);
     dst.m[li] = src.m[from];
     dst.qx[li] = src.qx[from];
     dst.qy[li] = src.qy[from];

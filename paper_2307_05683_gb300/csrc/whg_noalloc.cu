@@ -26,6 +26,9 @@ constexpr size_t kBytes = (8 * kLanes + 10 * kSystems) * sizeof(double) + kSyste
 // Device-side scratch.  In host code this name is only a host stand-in: its
 // device address comes from cudaGetSymbolAddress (per device, below).
 static __device__ __align__(256) unsigned char g_scratch[kBytes];
+#ifdef WHG_DEBUG_BOUNDS
+static __device__ unsigned g_noalloc_bounds;      // index-check flag of the debug build
+#endif
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
@@ -125,6 +128,16 @@ extern "C" int whg_integrate_noalloc(int n_systems, int max_planets, const whg_o
     st.nplan = ip; ip += P;
     st.status = ip;
     st.perm = nullptr;
+    st.nl = (long long)NL;
+    st.dbg = nullptr;
+#ifdef WHG_DEBUG_BOUNDS
+    {
+        void* flagp = nullptr;
+        if (cudaGetSymbolAddress(&flagp, g_noalloc_bounds) != cudaSuccess)
+            return noalloc_fail(WHG_ECUDA, "cudaGetSymbolAddress(bounds flag): %s", "");
+        st.dbg = (unsigned*)flagp;
+    }
+#endif
     st.S = n_systems;
     st.Nmax = max_planets;
     st.c_light = opt.c_light;

@@ -43,7 +43,8 @@ class whg_options(ctypes.Structure):
 
 
 def library_path() -> str:
-    return _build.LIB
+    """libwhg.so, or the library named by WHG_LIBRARY (e.g. the debug build)."""
+    return os.environ.get("WHG_LIBRARY") or _build.LIB
 
 
 def load():
@@ -52,7 +53,7 @@ def load():
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.LIB
+        path = library_path()
         if not os.path.exists(path):
             raise RuntimeError(f"libwhg.so not found at {path}: build it with "
                                "paper_2307_05683_gb300.build.build() (there is no CPU fallback)")
@@ -81,6 +82,7 @@ def load():
             "whg_probe_fp64_lanes": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                     ctypes.POINTER(ctypes.c_float)]),
             "whg_test_queue_timeout": (ctypes.c_int, [P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)]),
+            "whg_debug_bounds": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_uint)]),
             "whg_kepler_sweep": (ctypes.c_int, [D, D, I, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                                 ctypes.c_longlong, D, D]),
             "whg_adjoint_forward": (ctypes.c_int, [P, ctypes.c_longlong, ctypes.c_int, D, D]),
@@ -104,7 +106,8 @@ def exported_symbols() -> list[str]:
             "whg_energy_device", "whg_get_raw", "whg_set_raw", "whg_synchronize",
             "whg_launch_count", "whg_last_error", "whg_destroy", "whg_measure_fp64_tflops",
             "whg_test_special", "whg_integrate_noalloc", "whg_adjoint_forward",
-            "whg_adjoint_backward", "whg_kepler_sweep", "whg_probe_fp64_lanes", "whg_test_queue_timeout"]
+            "whg_adjoint_backward", "whg_kepler_sweep", "whg_probe_fp64_lanes", "whg_test_queue_timeout",
+            "whg_debug_bounds"]
 
 
 def _check(ctx, rc: int) -> None:
@@ -266,6 +269,13 @@ def whg_probe_fp64_lanes(warps_per_sm: int, active_lanes: int, iters: int) -> fl
     _check(None, load().whg_probe_fp64_lanes(int(warps_per_sm), int(active_lanes), int(iters),
                                              ctypes.byref(ms)))
     return float(ms.value)
+
+
+def whg_debug_bounds(ctx) -> int:
+    """Index-check flag bits of ctx since the last call (debug build only)."""
+    flag = ctypes.c_uint()
+    _check(ctx, load().whg_debug_bounds(ctx, ctypes.byref(flag)))
+    return int(flag.value)
 
 
 def whg_test_queue_timeout(ctx, spin_limit: int) -> int:
