@@ -108,11 +108,12 @@ def solar_copies(n_systems: int, seed: int = 0, dt_days: float = 5.0, perturb_m:
     return ens
 
 
-def energy_error_run(ens, total_steps: int, samples: int = 20, gr_mode: int = 1):
+def energy_error_run(ens, total_steps: int, samples: int = 20, gr_mode: int = 1, **options):
     """Relative energy error |E(t)/E(0) - 1| of every system at `samples`
-    evenly spaced times (whg_energy on the synchronized state).
+    evenly spaced times (whg_energy on the synchronized state); `options`
+    go to the Integrator (e.g. halley_fp32=True).
     Returns (times [samples], errors [samples, S], status [S])."""
-    it = whg.Integrator(ens.n_systems, ens.max_planets, gr_mode=gr_mode)
+    it = whg.Integrator(ens.n_systems, ens.max_planets, gr_mode=gr_mode, **options)
     it.init(ens)
     E0 = it.energy()
     chunk = max(1, total_steps // samples)
