@@ -7,8 +7,9 @@ e and i perturbed by Rayleigh(1e-3), angles seeded), dt = P_Mercury / 20, GR
 term on.  One benchmark step = one whg_step call advancing every system by
 --chunk integrator steps (default 1e4; 100 benchmark steps = the full 1e6
 steps).  The state lives in registers during a launch, so there is no
-per-step memory traffic to cache; L2 is flushed (256 MB write) between timed
-steps anyway.
+per-step memory traffic to cache (with the default work queue it is reloaded
+from L2 every 100 steps); L2 is flushed (256 MB write) between timed steps
+anyway.
 
 Prints ONE JSON line.  --impl reference times the CPU oracle instead (rank 0).
 Multi-GPU (torchrun): each rank integrates its own ensemble of the same size
@@ -93,7 +94,8 @@ def workload(args) -> dict:
                               "(8-term series) and f, g in FP64" if args.halley_fp32 else
                               "initial guess, 2 Halley steps (4-term series), 2 Newton steps (8-term series) "
                               "and f, g all in FP64"),
-            "l2": "state register-resident during a launch; 256 MB L2 flush between timed steps"}
+            "l2": "state register-resident during each 100-step work unit (reloaded from L2 between units); "
+                  "256 MB L2 flush between timed steps"}
 
 
 # ------------------------------------------------------------ environment --
