@@ -5,7 +5,6 @@ exchange between ranks."""
 import os
 import socket
 
-import numpy as np
 import pytest
 import torch.multiprocessing as mp
 
