@@ -12,7 +12,7 @@
 //     approximation of a mantissa built with integer operations and take one
 //     third-order FP64 refinement whose exact pieces (1 - x y, y^2, y^3) are
 //     formed on the integer pipe (1/x: 2, x^(-1/2) and x^(-3/2): 4 FP64
-//     instructions);
+//     instructions), and the solver's factors -1/2 are exponent decrements;
 //   * the all-pairs interaction uses Newton's third law (Sec. 3.3), with
 //     partner schedules that suit warp shuffles rather than AVX512 lanes;
 //   * cross-lane sums of 3-vectors are reduce-scatters by xor partners when L
@@ -94,6 +94,23 @@ __device__ __forceinline__ double exp_bits_to_double(long long E, unsigned long 
     const unsigned long long bits = E >= 0x7ff ? 0x7ff0000000000000ULL
                                   : (E <= 0 ? 0ULL : (((unsigned long long)E << 52) | f));
     return __longlong_as_double((long long)bits);
+}
+
+// -x/2 exactly, on the integer pipe: an exponent decrement and a sign flip
+// for normal x; zero, subnormal and the smallest normals halve their
+// significand with round-to-nearest-even (the result's encoding follows from
+// the carry); inf and NaN keep their exponent.  Equal to -0.5 * x.
+__device__ __forceinline__ double neg_half(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long sign = (b ^ 0x8000000000000000ULL) & 0x8000000000000000ULL;
+    const unsigned long long ex = (b >> 52) & 0x7ffULL;
+    const unsigned long long f = b & 0x000fffffffffffffULL;
+    const unsigned long long M = ex == 1ULL ? (f | 0x0010000000000000ULL) : f;   // subnormal-scale significand
+    const unsigned long long half = (M >> 1) + (M & (M >> 1) & 1ULL);            // M/2, ties to even
+    const unsigned long long normal = (b - 0x0010000000000000ULL) & 0x7fffffffffffffffULL;
+    const unsigned long long mag = ex >= 2ULL ? (ex == 0x7ffULL ? (b & 0x7fffffffffffffffULL) : normal) : half;
+    return __longlong_as_double((long long)(sign | mag));
 }
 
 // 53-bit significand of a finite normal double as an integer.
@@ -349,7 +366,7 @@ __device__ __forceinline__ bool kepler_drift(double mu, double h, double& qx, do
         X = to_f64(Xs);
     } else {
         const double hr = h * r0i;
-        X = fma(-0.5 * eta0 * hr * hr, r0i, hr);
+        X = fma(neg_half(eta0) * hr * hr, r0i, hr);
 #pragma unroll
         for (int it = 0; it < 2; ++it) {             // Halley
             X2 = X * X;
@@ -359,7 +376,7 @@ __device__ __forceinline__ bool kepler_drift(double mu, double h, double& qx, do
             const double F = fma(r0, X, fma(eta0, G2, fma(zeta0, G3, -h)));
             const double Fp = fma(zeta0, G2, fma(-beta_eta0, G3, fma(eta0, X, r0)));
             const double Fpp = fma(-beta_zeta0, G3, fma(-beta_eta0, G2, fma(zeta0, X, eta0)));
-            const double den = fma(-0.5 * F, Fpp, Fp * Fp);      // (2F'^2 - F F'') / 2
+            const double den = fma(neg_half(F), Fpp, Fp * Fp);   // (2F'^2 - F F'') / 2
             X = fma(-(F * Fp), rcp(den), X);
         }
     }
