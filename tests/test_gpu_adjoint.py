@@ -61,9 +61,10 @@ def _targets(ens, seed, spread=0.05):
     return T * live[..., None]
 
 
-@pytest.mark.parametrize("gr_mode,merge,h32", [(0, False, False), (1, False, False), (2, False, False),
-                                               (0, True, False), (1, False, True)])
-def test_adjoint_matches_oracle_tangent(whg, orc, gr_mode, merge, h32):
+@pytest.mark.parametrize("gr_mode,merge,h32,sched", [(0, False, False, 0), (1, False, False, 0),
+                                                     (2, False, False, 0), (0, True, False, 0),
+                                                     (1, False, True, 0), (1, False, False, 1)])
+def test_adjoint_matches_oracle_tangent(whg, orc, gr_mode, merge, h32, sched):
     """Every input direction of a few systems (8-planet and compact mixed),
     1000 steps, checkpoints every 100: the adjoint equals the oracle's
     forward-mode derivative to 1e-8 of the largest gradient entry."""
@@ -75,7 +76,7 @@ def test_adjoint_matches_oracle_tangent(whg, orc, gr_mode, merge, h32):
     T = _targets(both, 1)
     n = 1000
     loss, gx, gu, gm = gpu_grad(whg, both, T, n, 100, gr_mode=gr_mode, merge_jumps=merge,
-                                  halley_fp32=h32)
+                                  halley_fp32=h32, interaction_schedule=sched)
     for s in range(both.n_systems):
         k = int(both.n_planets[s])
         L, tx, tu, tm = orc.tangent_gradient(both.masses[s], both.pos[s], both.vel[s], k, both.dt[s], T[s],
