@@ -136,7 +136,8 @@ typedef struct {
                                  Results are bitwise the same either way.  A wait that exceeds
                                  its limit (seconds; only possible after a fault) makes the
                                  next whg_synchronize or whg_read_state return WHG_ECUDA.  Not
-                                 part of the paper's method. */
+                                 part of the paper's method.  Ignored by
+                                 whg_integrate_noalloc (plain launches). */
 } whg_options;
 
 /* Fill *opt with the defaults above. */
