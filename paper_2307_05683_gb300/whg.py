@@ -210,6 +210,9 @@ def whg_energy_device(ctx, E) -> None:
 
 
 def whg_get_raw(ctx, Q: np.ndarray, v: np.ndarray, nstep: np.ndarray, status: np.ndarray) -> None:
+    for a, dt in ((Q, np.float64), (v, np.float64), (nstep, np.int64), (status, np.int32)):
+        if a.dtype != dt or not a.flags.c_contiguous:
+            raise ValueError("output arrays must be C-contiguous with the documented dtypes")
     _check(ctx, load().whg_get_raw(ctx, Q.ctypes.data, v.ctypes.data, nstep.ctypes.data,
                                    status.ctypes.data))
 
@@ -355,7 +358,18 @@ class Integrator:
     def __exit__(self, *exc):
         self.close()
 
+    def _check_shapes(self, arrays) -> None:
+        """The C calls read S x (...) elements from each host array; refuse
+        arrays of any other shape before they are read past their end."""
+        for name, a, shape in arrays:
+            if np.shape(a) != shape:
+                raise ValueError(f"{name} has shape {np.shape(a)}, expected {shape}")
+
     def init(self, ens) -> None:
+        S, B = self.S, 1 + self.N
+        self._check_shapes((("masses", ens.masses, (S, B)), ("pos", ens.pos, (S, B, 3)),
+                            ("vel", ens.vel, (S, B, 3)), ("n_planets", ens.n_planets, (S,)),
+                            ("dt", ens.dt, (S,))))
         whg_init(self.ctx, ens.masses, ens.pos, ens.vel, ens.n_planets, ens.dt)
 
     def step(self, n: int) -> None:
@@ -383,6 +397,9 @@ class Integrator:
         return Q, v, ns, st
 
     def set_raw(self, Q, v, nstep, status) -> None:
+        S, N = self.S, self.N
+        self._check_shapes((("Q", Q, (S, N, 3)), ("v", v, (S, N, 3)), ("nstep", nstep, (S,)),
+                            ("status", status, (S,))))
         whg_set_raw(self.ctx, Q, v, nstep, status)
 
     def synchronize(self) -> None:

@@ -111,3 +111,28 @@ def test_solar_copies_perturbation():
     assert np.all(np.abs(shift_m) <= 2.0 * (1 + 1e-6)) and np.std(shift_m) > 0.5
     np.testing.assert_array_equal(ens.dt, 4.0 * inputs.DAY)
 
+
+
+def test_integrator_refuses_misshaped_host_arrays():
+    """Integrator.init and set_raw check every host array's shape against the
+    context's S and N before any library call (no GPU needed to reach the check)."""
+    import pytest
+    from paper_2307_05683_gb300 import whg
+    it = object.__new__(whg.Integrator)
+    it.S, it.N, it.ctx = 4, 2, None
+    good = inputs.two_planet_system(0, 4)
+    for bad in (inputs.two_planet_system(0, 3), inputs.solar_ensemble(0, 4)):
+        with pytest.raises(ValueError):
+            it.init(bad)
+    short = inputs.two_planet_system(0, 4)
+    short.dt = short.dt[:3]
+    with pytest.raises(ValueError, match="dt"):
+        it.init(short)
+    Q = np.zeros((4, 2, 3))
+    with pytest.raises(ValueError, match="v"):
+        it.set_raw(Q, np.zeros((4, 3, 3)), np.zeros(4, np.int64), np.zeros(4, np.int32))
+    with pytest.raises(ValueError, match="status"):
+        it.set_raw(Q, Q, np.zeros(4, np.int64), np.zeros(5, np.int32))
+    it._check_shapes((("masses", good.masses, (4, 3)), ("pos", good.pos, (4, 3, 3))))
+    with pytest.raises(ValueError):
+        whg.whg_get_raw(None, Q, Q, np.zeros(4, np.int32), np.zeros(4, np.int32))
