@@ -21,6 +21,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liborc.so")
+# A prebuilt oracle library to load instead of _LIB: the planted-mistake tests
+# (tests/test_oracle_mutations.py) point this at a copy built with one change.
+_LIB_OVERRIDE = os.environ.get("ORC_LIBRARY")
 _FLOPS = os.path.join(_BUILD, "orc_flopcount")
 _TANGENT = os.path.join(_BUILD, "liborc_tangent.so")
 _SOURCES = [os.path.join(_HERE, f) for f in ("orc_core.c", "orc_ensemble.c", "flopcount.cpp",
@@ -39,16 +42,22 @@ def _stale(target: str) -> bool:
     return any(os.path.getmtime(s) > t for s in _SOURCES)
 
 
+def compile_library(source_dir: str, out: str) -> None:
+    """gcc the oracle library from orc_ensemble.c (which includes orc_core.c)
+    in source_dir into out."""
+    tmp = out + f".{os.getpid()}.tmp"
+    subprocess.check_call(["gcc", "-std=c99", "-D_POSIX_C_SOURCE=200809L", "-O2",
+                           "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                           "-o", tmp, os.path.join(source_dir, "orc_ensemble.c"),
+                           "-lpthread", "-lm"])
+    os.replace(tmp, out)
+
+
 def build(force: bool = False) -> None:
     """Compile the oracle library and the flop counter with gcc / g++."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or _stale(_LIB):
-        tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-std=c99", "-D_POSIX_C_SOURCE=200809L", "-O2",
-                               "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-                               "-o", tmp, os.path.join(_HERE, "orc_ensemble.c"),
-                               "-lpthread", "-lm"])
-        os.replace(tmp, _LIB)
+        compile_library(_HERE, _LIB)
     if force or _stale(_FLOPS):
         tmp = _FLOPS + f".{os.getpid()}.tmp"
         subprocess.check_call(["g++", "-O2", "-ffp-contract=off", "-o", tmp,
@@ -66,8 +75,11 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        build()
-        lib = ctypes.CDLL(_LIB)
+        if _LIB_OVERRIDE:
+            lib = ctypes.CDLL(_LIB_OVERRIDE)
+        else:
+            build()
+            lib = ctypes.CDLL(_LIB)
         P = ctypes.c_void_p
         D = ctypes.POINTER(ctypes.c_double)
         I = ctypes.POINTER(ctypes.c_int)
