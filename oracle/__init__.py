@@ -24,6 +24,7 @@ _LIB = os.path.join(_BUILD, "liborc.so")
 # A prebuilt oracle library to load instead of _LIB: the planted-mistake tests
 # (tests/test_oracle_mutations.py) point this at a copy built with one change.
 _LIB_OVERRIDE = os.environ.get("ORC_LIBRARY")
+_TANGENT_OVERRIDE = os.environ.get("ORC_TANGENT_LIBRARY")   # the same for the tangent build
 _FLOPS = os.path.join(_BUILD, "orc_flopcount")
 _TANGENT = os.path.join(_BUILD, "liborc_tangent.so")
 _SOURCES = [os.path.join(_HERE, f) for f in ("orc_core.c", "orc_ensemble.c", "flopcount.cpp",
@@ -53,6 +54,15 @@ def compile_library(source_dir: str, out: str) -> None:
     os.replace(tmp, out)
 
 
+def compile_tangent(source_dir: str, out: str) -> None:
+    """g++ the dual-number build (tangent.cpp, which includes orc_core.c) in
+    source_dir into out."""
+    tmp = out + f".{os.getpid()}.tmp"
+    subprocess.check_call(["g++", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp,
+                           os.path.join(source_dir, "tangent.cpp")])
+    os.replace(tmp, out)
+
+
 def build(force: bool = False) -> None:
     """Compile the oracle library and the flop counter with gcc / g++."""
     os.makedirs(_BUILD, exist_ok=True)
@@ -64,10 +74,7 @@ def build(force: bool = False) -> None:
                                os.path.join(_HERE, "flopcount.cpp")])
         os.replace(tmp, _FLOPS)
     if force or _stale(_TANGENT):
-        tmp = _TANGENT + f".{os.getpid()}.tmp"
-        subprocess.check_call(["g++", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp,
-                               os.path.join(_HERE, "tangent.cpp")])
-        os.replace(tmp, _TANGENT)
+        compile_tangent(_HERE, _TANGENT)
 
 
 def _load():
@@ -212,8 +219,11 @@ def _load_tangent():
     global _tlib
     with _lock:
         if _tlib is None:
-            build()
-            lib = ctypes.CDLL(_TANGENT)
+            if _TANGENT_OVERRIDE:
+                lib = ctypes.CDLL(_TANGENT_OVERRIDE)
+            else:
+                build()
+                lib = ctypes.CDLL(_TANGENT)
             D = ctypes.POINTER(ctypes.c_double)
             lib.orc_tangent_loss.argtypes = [ctypes.c_int, D, D, D, ctypes.c_double, D, ctypes.c_longlong,
                                              ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,

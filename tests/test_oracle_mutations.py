@@ -10,7 +10,10 @@ built the same way, to pass them all.  The one check that compares the
 oracle with itself (fused drifts against single sub-steps) is left out; the
 remaining pins are independent of the oracle (closed forms, brute force,
 conservation laws, exact orbits, a high-order reference integration), so
-this shows that they constrain each part of the map.  CPU only.
+this shows that they constrain each part of the map.  The dual-number build
+that gives the adjoint's reference gradients gets the same treatment for its
+derivative rules, against its own pins (central differences of the plain
+oracle, invariances of the loss).  CPU only.
 """
 import concurrent.futures
 import os
@@ -74,6 +77,18 @@ MUTATIONS = {
     "eject_radius_unscaled": ("orc_core.c", "rej *= opt->eject_factor;", "rej *= 1.0;"),
 }
 
+# Derivative rules of the dual-number build that gives the adjoint's reference
+# gradients (oracle/tangent.cpp); pinned by tests/test_oracle_tangent.py.
+TANGENT_PINS = ["tests/test_oracle_tangent.py"]
+TANGENT_MUTATIONS = {
+    "product_rule_one_term": ("tangent.cpp", "a.d * b.v + a.v * b.d)", "a.d * b.v)"),
+    "quotient_rule_sign": ("tangent.cpp", "(a.d * b.v - a.v * b.d) / (b.v * b.v)", "(a.d * b.v + a.v * b.d) / (b.v * b.v)"),
+    "sqrt_derivative_factor": ("tangent.cpp", "Dual(r, x.d / (2.0 * r))", "Dual(r, x.d / r)"),
+    "negation_derivative": ("tangent.cpp", "return Dual(-a.v, -a.d);", "return Dual(-a.v, a.d);"),
+    "mass_direction_seed": ("tangent.cpp", "md[k] = Dual(m[k], (kind == 2 && body == k) ? 1.0 : 0.0);",
+                            "md[k] = Dual(m[k], 0.0);"),
+}
+
 
 def _build(name, workdir):
     """Copy the oracle's C sources, plant one mistake (name "unchanged":
@@ -82,23 +97,29 @@ def _build(name, workdir):
     src = os.path.join(workdir, name)
     os.makedirs(src)
     for f in os.listdir(os.path.join(ROOT, "oracle")):
-        if f.endswith((".c", ".h")):
+        if f.endswith((".c", ".cpp", ".h")):
             shutil.copy(os.path.join(ROOT, "oracle", f), src)
-    if name != "unchanged":
-        f, old, new = MUTATIONS[name]
+    tangent = name in TANGENT_MUTATIONS or name == "unchanged_tangent"
+    if not name.startswith("unchanged"):
+        f, old, new = (TANGENT_MUTATIONS if tangent else MUTATIONS)[name]
         path = os.path.join(src, f)
         text = open(path).read()
         assert text.count(old) == 1, f"{name}: the original text must occur exactly once in {f}"
         open(path, "w").write(text.replace(old, new))
-    lib = os.path.join(src, "liborc.so")
-    oracle.compile_library(src, lib)
+    if tangent:
+        lib = os.path.join(src, "liborc_tangent.so")
+        oracle.compile_tangent(src, lib)
+    else:
+        lib = os.path.join(src, "liborc.so")
+        oracle.compile_library(src, lib)
     return lib
 
 
-def _run_pins(lib):
-    env = dict(os.environ, ORC_LIBRARY=lib)
+def _run_pins(lib, tangent=False):
+    env = dict(os.environ, **({"ORC_TANGENT_LIBRARY": lib} if tangent else {"ORC_LIBRARY": lib}))
+    pins = TANGENT_PINS if tangent else PINS
     deselect = [a for t in SELF_CHECKS for a in ("--deselect", t)]
-    r = subprocess.run([sys.executable, "-m", "pytest", *PINS, *deselect, "-x", "-q", "-m", "not gpu",
+    r = subprocess.run([sys.executable, "-m", "pytest", *pins, *deselect, "-x", "-q", "-m", "not gpu",
                         "-p", "no:cacheprovider"], cwd=ROOT, env=env, capture_output=True, text=True,
                        timeout=600)
     failed = [ln.split(" ")[1] for ln in r.stdout.splitlines() if ln.startswith("FAILED ")]
@@ -106,23 +127,25 @@ def _run_pins(lib):
 
 
 def test_every_planted_mistake_fails_a_pin(tmp_path, orc):
-    names = ["unchanged", *MUTATIONS]
+    names = ["unchanged", "unchanged_tangent", *MUTATIONS, *TANGENT_MUTATIONS]
     workers = max(2, min(8, os.cpu_count() or 2))
 
     def one(name):
-        return name, _run_pins(_build(name, str(tmp_path)))
+        tangent = name in TANGENT_MUTATIONS or name == "unchanged_tangent"
+        return name, _run_pins(_build(name, str(tmp_path)), tangent)
 
     with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
         results = dict(ex.map(one, names))
-    rc, failed, tail = results.pop("unchanged")
-    assert rc == 0, f"the unchanged copy must pass every pin:\n{tail}"
+    for control in ("unchanged", "unchanged_tangent"):
+        rc, failed, tail = results.pop(control)
+        assert rc == 0, f"the unchanged copy ({control}) must pass every pin:\n{tail}"
     survivors = {n: tail for n, (rc, failed, tail) in results.items() if rc != 1 or not failed}
     assert not survivors, "planted mistakes that no pin caught: " + ", ".join(survivors)
 
 
-@pytest.mark.parametrize("name", sorted(MUTATIONS))
+@pytest.mark.parametrize("name", sorted(MUTATIONS) + sorted(TANGENT_MUTATIONS))
 def test_mutation_text_is_present(name):
     """Each planted mistake still finds its original text (the list follows
     the oracle's source)."""
-    f, old, new = MUTATIONS[name]
+    f, old, new = {**MUTATIONS, **TANGENT_MUTATIONS}[name]
     assert open(os.path.join(ROOT, "oracle", f)).read().count(old) == 1 and old != new
