@@ -99,3 +99,58 @@ def test_create_rejects_bad_sizes(lib_path):
     assert lib.whg_create(ctypes.byref(h), 0, 8, None, None) == whg.WHG_EINVAL
     assert lib.whg_create(ctypes.byref(h), 4, 9, None, None) == whg.WHG_EINVAL
     assert lib.whg_create(None, 4, 8, None, None) == whg.WHG_EINVAL
+
+
+def _functions_importing(path, module):
+    """Names of the top-level functions of a Python file that import `module`
+    (None for an import at module level)."""
+    import ast
+    found = set()
+    for top in ast.parse(open(path).read()).body:
+        owner = top.name if isinstance(top, (ast.FunctionDef, ast.AsyncFunctionDef)) else None
+        for node in ast.walk(top):
+            if isinstance(node, ast.Import) and any(a.name.split(".")[0] == module for a in node.names):
+                found.add(owner)
+            if isinstance(node, ast.ImportFrom) and (node.module or "").split(".")[0] == module:
+                found.add(owner)
+    return found
+
+
+def test_product_path_never_reaches_the_oracle():
+    """The package and its CUDA sources neither import, include nor name the
+    oracle; bench.py imports it only in its CPU-baseline and reference legs,
+    __graft_entry__ only to build it and in smoke()."""
+    pkg = os.path.join(ROOT, "paper_2307_05683_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        if "_build" in dirpath:
+            continue
+        for f in files:
+            if f.endswith(".py"):
+                assert not _functions_importing(os.path.join(dirpath, f), "oracle"), f
+            if f.endswith((".cu", ".cuh", ".h", ".py")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"\borc_[a-z]|liborc|#include\s+\"[^\"]*orc", text), f
+    assert _functions_importing(os.path.join(ROOT, "bench.py"), "oracle") == {"oracle_rate", "run_reference"}
+    assert _functions_importing(os.path.join(ROOT, "__graft_entry__.py"), "oracle") == {"build", "smoke"}
+    # the one call of the oracle's timing in the GPU arm fills only cpu_baseline
+    lines = open(os.path.join(ROOT, "bench.py")).read().splitlines()
+    calls = [k for k, ln in enumerate(lines) if "oracle_rate(" in ln and not ln.startswith("def ")]
+    assert len(calls) == 1 and lines[calls[0] + 1].strip().startswith('line["cpu_baseline"]')
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """With no libwhg.so at the configured path every call raises (there is
+    no CPU fallback)."""
+    code = ("from paper_2307_05683_gb300 import whg\n"
+            "for call in (whg.whg_default_options, lambda: whg.Integrator(4, 2)):\n"
+            "    try:\n"
+            "        call()\n"
+            "    except RuntimeError as e:\n"
+            "        assert 'no CPU fallback' in str(e), e\n"
+            "    else:\n"
+            "        raise SystemExit('a call succeeded without the library')\n"
+            "print('ok')\n")
+    env = dict(os.environ, WHG_LIBRARY=str(tmp_path / "absent" / "libwhg.so"))
+    r = subprocess.run([os.sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
