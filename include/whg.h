@@ -75,7 +75,10 @@ typedef struct {
                                  default 10065.32 */
     int newton_terms;         /* Stumpff series terms in the Newton phase: 8 (default,
                                  Sec. 3.2) or 6 (Appendix A).  The Halley phase always
-                                 uses 4 terms; 2 Halley + 2 Newton iterations (Sec. 3.2). */
+                                 uses 4 terms; 2 Halley + 2 Newton iterations (Sec. 3.2).
+                                 T terms: c_2, c_3 summed through the z^T term,
+                                 c_n(z) ~ sum_{k=0..T} (-z)^k / (n+2k)!.  The initial
+                                 guess is X = h/r0. */
     int lanes_per_system;     /* 0 = auto: systems are grouped by planet count n and a
                                  system gets n warp lanes (8 for n = 7), floor(32/n)
                                  systems per warp, all groups in one launch.  1..8
@@ -107,7 +110,9 @@ typedef struct {
                                  (pericentre timescale below ~2 steps) both are inaccurate and
                                  may stop differently.  Default 0: the whole solver in FP64
                                  (the paper's arithmetic). */
-    int repack_frozen;        /* 1: every graph_launches step launches (every 16 without
+    int repack_frozen;        /* -1 (default): on when a stop rule is on
+                                 (close_encounter_hill > 0 or eject_factor > 0), else off.
+                                 1: every graph_launches step launches (every 16 without
                                  graphs; inside the captured graph with them) regroup the
                                  systems of each planet count so that running systems come
                                  first and stopped ones (status != 0) last.  A warp whose
@@ -117,7 +122,7 @@ typedef struct {
                                  repacking.  Costs a second copy of the state in device
                                  memory (allocated by whg_create).  Not part of the
                                  paper's method.  Ignored by whg_integrate_noalloc.
-                                 Default 0. */
+                                 0: off. */
     int interaction_schedule; /* 0 (default): pairs at lane distance k < L/2 evaluated once
                                  with the reaction passed back (Newton's third law, Sec. 3.3),
                                  distance L/2 by both lanes: 4 reciprocal square roots per lane
@@ -266,8 +271,9 @@ void whg_destroy(whg_ctx* ctx);
  * Limit: the warps needed (floor(32 / lanes) systems each) must not exceed
  * WHG_NOALLOC_MAX_LANES / 32 lanes' worth, e.g. 8192 systems of 7 or 8
  * planets; larger requests fail with WHG_EINVAL.
- * The first call on each device looks up the array's device address; make
- * that first call before any stream capture.
+ * Every call looks up the array's device address (no allocation); the first
+ * lookup on a device may load the library's device image, so make the first
+ * call on each device before any stream capture.
  * Every call reuses the same array and leaves its contents behind; each call
  * rewrites everything it reads before reading it.  Calls whose GPU work
  * overlaps (other streams, other host threads) race on the array: order them.
@@ -281,15 +287,20 @@ int whg_integrate_noalloc(int n_systems, int max_planets, const whg_options* opt
 
 /* ---- diagnostics (not part of the integration path) -------------------- */
 
-/* FP64 pipe throughput: runs a dependent-FMA loop on every SM of the current
- * device for about `seconds` and returns achieved FP64 TFLOP/s (FMA = 2
- * flops).  Blocks. */
+/* FP64 FMA-stream throughput: runs a loop of independent dependent-FMA
+ * chains on every SM of the current device for about `seconds` and returns
+ * the achieved FP64 TFLOP/s (FMA = 2 flops).  Blocks.  A diagnostic, not a
+ * peak: on GB300 a pure stream of DFMA, DMUL or DADD instructions issues at
+ * about 1.68 FP64 lanes per clock per SM however many warps and chains run,
+ * while the step kernel, whose FP64 instructions are interleaved with
+ * integer, shuffle and MUFU work, sustains about 1.8. */
 int whg_measure_fp64_tflops(double seconds, double* tflops);
 
 /* Solver search of Appendix A: n massless particles (DEVICE q, v [n][3]) each
  * drifted `steps` times by time h around a central mass mu with its own
  * solver configuration cfg [n][4] = (Halley iterations, Halley series terms,
- * Newton iterations, Newton series terms), terms 1..12; G_n after the last
+ * Newton iterations, Newton series terms), terms 1..12 (series through z^T,
+ * as newton_terms above), initial guess h/r0; G_n after the last
  * iteration evaluated at the final X with the Newton series length.  Plain
  * per-particle loops (a validation tool, not the integration path).
  * Writes q_out, v_out (DEVICE).  Blocks. */
@@ -324,6 +335,13 @@ int whg_test_queue_timeout(whg_ctx* ctx, long long spin_limit, int* flag);
  * ctx's stream, writes the bits set since the last call to *flag and clears
  * them.  In the release build: *flag = 0 and WHG_EINVAL. */
 int whg_debug_bounds(whg_ctx* ctx, unsigned* flag);
+
+/* The same index-check flags for whg_integrate_noalloc, whose checks record
+ * into one flag word of its own (no context): synchronizes the current
+ * device, writes the bits set by all calls since the last read to *flag and
+ * clears them.  Allocates nothing.  In the release build: *flag = 0 and
+ * WHG_EINVAL (message in whg_last_error(NULL)). */
+int whg_noalloc_debug_bounds(unsigned* flag);
 
 /* The library's own reciprocal, reciprocal square root and FP64 <-> FP32
  * conversions next to CUDA's, for testing: out [10][n] DEVICE buffer receives

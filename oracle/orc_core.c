@@ -10,7 +10,7 @@
  * democratic heliocentric coordinates (Sec. 3.1, Eq. 1 and Eq. 2), built from
  *   - the Kepler drift H_K (Sec. 3.2, Eq. 3): fixed 2 Halley + 2 Newton
  *     iterations on the universal-variable Kepler equation, Stumpff series
- *     truncated at 4 terms (Halley) and 8 (or 6, Appendix A) terms (Newton),
+ *     with 4 terms (Halley) and 8 (or 6, Appendix A) terms (Newton),
  *   - the jump step H_J (Sec. 3.4, Eq. 6),
  *   - the interaction kick H_I (Sec. 3.3, Eq. 5),
  *   - the optional 1/r^2 "GR" potential centred on the star (Sec. 3.3, last
@@ -19,11 +19,24 @@
  * sums); nothing is blocked, fused or reordered.  Build with -O2 -ffp-contract=off so that no
  * multiply-add is contracted.
  *
- * Readings where the paper is silent (listed with reasons in the design notes):
+ * Readings where the paper is silent:
  *   - Kepler mu = G m_0 (H_K of Eq. 3 uses G m_0 m_i, not G(m_0+m_i)).
- *   - initial guess X_0 = h/r_0 - eta_0 h^2 / (2 r_0^3) (second-order series).
- *   - "T terms" = T terms each of the c_2 and c_3 series; c_0, c_1 follow from
- *     c_0 = 1 - z c_2, c_1 = 1 - z c_3.
+ *   - initial guess X_0 = h / r_0 (the first-order value of X(h) = int dt/r;
+ *     the paper gives no guess).  Of the guesses tried (0, first and second
+ *     order), only this one makes 2 Halley steps need 2 Newton steps, as
+ *     Appendix A states; with the second-order guess one Newton step is on
+ *     the edge of the requirement.
+ *   - "T terms" = the series of c_2 and c_3 carried through the z^T term:
+ *     c_n(z) ~ sum_{k=0..T} (-z)^k / (n+2k)!, i.e. T terms after the leading
+ *     1/n! (equivalently T terms each of the c_4, c_5 series, with
+ *     c_2 = 1/2 - z c_4 and c_3 = 1/6 - z c_5); c_0, c_1 follow from
+ *     c_0 = 1 - z c_2, c_1 = 1 - z c_3.  With this count the main text's
+ *     default (4 and 8 terms) meets Appendix A's requirement (relative a
+ *     error below 1e-13 at a = 0.387 AU, 5-day step, 10 yr, e <= 0.7) and
+ *     8 is the shortest Newton-phase series that does; counting the leading
+ *     term as one of the T (T terms in all), it misses at e = 0.7 by a
+ *     factor of 2.  Appendix A's 6 terms miss the requirement under every
+ *     count tried (5.8e-11 at e = 0.7 with this one).
  *   - f, g, fdot, gdot use G_n re-evaluated at the final X (T_N terms).
  *   - GR: Phi(r) = -3 (G m_0)^2 / (c^2 r^2) per unit planet mass.  gr_mode 1
  *     kicks v_i by h a_GR(Q_i) (canonical in these coordinates); gr_mode 2 also
@@ -106,7 +119,7 @@ typedef struct {
 } orc_system;
 
 /* 1/k! for the Stumpff series: k! is exact in double for k <= 22, so one
- * division rounds it correctly. */
+ * division rounds it correctly (the default 8-term series needs k <= 19). */
 static double orc_inv_factorial(int k)
 {
     double f = 1.0;
@@ -116,14 +129,15 @@ static double orc_inv_factorial(int k)
 }
 
 /* Stumpff functions c_2(z), c_3(z) by their Taylor series truncated after
- * `terms` terms, c_n(z) = sum_k (-z)^k / (n+2k)!, evaluated by Horner's rule
- * (Sec. 3.2: series plus a precomputed table, no quarter-angle reduction). */
+ * the z^terms term, c_n(z) = sum_{k=0..terms} (-z)^k / (n+2k)!, evaluated by
+ * Horner's rule (Sec. 3.2: series plus a precomputed table, no quarter-angle
+ * reduction). */
 static void orc_stumpff_c2c3(orc_real z, int terms, orc_real* c2, orc_real* c3)
 {
-    orc_real s2 = orc_inv_factorial(2 * terms);      /* k = terms-1: 1/(2+2k)! */
-    orc_real s3 = orc_inv_factorial(2 * terms + 1);  /* 1/(3+2k)! */
+    orc_real s2 = orc_inv_factorial(2 * terms + 2);  /* k = terms: 1/(2+2k)! */
+    orc_real s3 = orc_inv_factorial(2 * terms + 3);  /*            1/(3+2k)! */
     int k;
-    for (k = terms - 2; k >= 0; --k) {
+    for (k = terms - 1; k >= 0; --k) {
         s2 = orc_inv_factorial(2 * k + 2) - z * s2;
         s3 = orc_inv_factorial(2 * k + 3) - z * s3;
     }
@@ -167,7 +181,7 @@ static void orc_kepler_drift(orc_mass mu, double h, orc_real Q[3], orc_real v[3]
     int it;
     *beta_out = beta;
     ORC_START_PHASE(1);
-    X = h / r0 - eta0 * h * h / (2.0 * r0 * r0 * r0);
+    X = h / r0;
 
     for (it = 0; it < opt->halley_iters; ++it) {           /* Halley's method */
         orc_stiefel(beta, X, opt->halley_terms, G);

@@ -53,8 +53,8 @@ __device__ __forceinline__ double stumpff_c(double z)
 // = adjoints of Q0, v0; lmu accumulates the adjoint of mu.
 //
 // c4, c5 come from their NT-term series and c2 = 1/2 - z c4, c3 = 1/6 - z c5
-// from the recurrence (one more term of c2, c3 than the forward drift sums:
-// a change of ~z^NT/(2NT+2)!, far below the gradient's accuracy).  Every
+// from the recurrence: the same series through z^NT that the forward drift
+// sums.  Every
 // Lagrange coefficient is mu times a function of the G_n, so the adjoints of
 // mu, r, r0 and G_n are written with f - 1, fdot and gdot - 1 themselves:
 //   mub  = ((f-1) fb + fdot fdb + (gdot-1) gdb) / mu - G3 gb,

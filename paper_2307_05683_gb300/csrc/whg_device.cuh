@@ -3,7 +3,7 @@
 // warp lanes per system (one lane per planet, L in 1..8, floor(32/L) systems
 // per warp).
 //
-// GB300 design notes.  The whole step is FP64 arithmetic on a few registers
+// Why the code looks as it does.  The whole step is FP64 arithmetic on a few registers
 // per lane; on this part the FP64 pipe retires about 2 lanes per clock per SM
 // while FP32, integer, shuffle and MUFU work retire tens of times faster.  So
 // the step is bound by the number of FP64 instructions alone, and the code
@@ -249,11 +249,11 @@ __device__ __forceinline__ bool is_finite(double x)
 }
 
 // ------------------------------------------------------------------------
-// Stumpff functions c_2(z), c_3(z) by their Taylor series truncated after T
-// terms, c_n(z) = sum_{k<T} (-z)^k / (n+2k)! (Sec. 3.2: series with a table of
-// coefficients, no quarter-angle reduction).  The coefficients 1/k! are
-// compile-time constants: k! is exact in double for k <= 22, and the compiler
-// rounds 1/k! once.
+// Stumpff functions c_2(z), c_3(z) by their T-term Taylor series, carried
+// through the z^T term: c_n(z) = sum_{k<=T} (-z)^k / (n+2k)! (Sec. 3.2: series
+// with a table of coefficients, no quarter-angle reduction; T terms after the
+// leading 1/n!).  The coefficients 1/k! are compile-time constants: k! is
+// exact in double for k <= 22, and the compiler rounds 1/k! once.
 
 template <int N>
 struct Factorial {
@@ -281,9 +281,9 @@ struct StumpffHorner<-1> {
 template <int T>
 __device__ __forceinline__ void stumpff_c2c3(double z, double& c2, double& c3)
 {
-    c2 = 1.0 / Factorial<2 * T>::value;          // term k = T-1
-    c3 = 1.0 / Factorial<2 * T + 1>::value;
-    StumpffHorner<T - 2>::run(z, c2, c3);
+    c2 = 1.0 / Factorial<2 * T + 2>::value;      // term k = T
+    c3 = 1.0 / Factorial<2 * T + 3>::value;
+    StumpffHorner<T - 1>::run(z, c2, c3);
 }
 
 // The same series in FP32 (coefficients 1/k! rounded to float), for the
@@ -305,9 +305,9 @@ struct StumpffHornerF<-1> {
 template <int T>
 __device__ __forceinline__ void stumpff_c2c3_f32(float z, float& c2, float& c3)
 {
-    c2 = (float)(1.0 / Factorial<2 * T>::value);
-    c3 = (float)(1.0 / Factorial<2 * T + 1>::value);
-    StumpffHornerF<T - 2>::run(z, c2, c3);
+    c2 = (float)(1.0 / Factorial<2 * T + 2>::value);
+    c3 = (float)(1.0 / Factorial<2 * T + 3>::value);
+    StumpffHornerF<T - 1>::run(z, c2, c3);
 }
 
 
@@ -315,15 +315,16 @@ __device__ __forceinline__ void stumpff_c2c3_f32(float z, float& c2, float& c3)
 // Kepler drift of one planet for time h under H_K,i (Sec. 3.2, Eq. 3),
 // mu = G m0.  Universal variable X solves Kepler's equation
 //     F(X)  = r0 G1 + eta0 G2 + mu G3 - h = r0 X + eta0 G2 + zeta0 G3 - h = 0,
-//     F'(X) = r = r0 + eta0 X + zeta0 G2 - beta eta0 G3,
-//     F''   = eta0 + zeta0 X - beta eta0 G2 - beta zeta0 G3
+//     F'(X) = r = r0 + eta0 G1 + zeta0 G2,
+//     F''   = eta0 G0 + zeta0 G1
 // (the second forms use G0 = 1 - beta G2, G1 = X - beta G3 and
 // zeta0 = mu - beta r0, so only the c2 and c3 series are needed): initial
-// guess h/r0 - eta0 h^2 / (2 r0^3), 2 Halley steps with 4-term series, 2 Newton
-// steps with NT-term series.  The G_n at the final X = X1 + d come from the
-// values at the last Newton point X1 by one Taylor step (dG_n/dX = G_{n-1});
-// |d| is the last Newton correction, so the neglected d^2 terms are far below
-// rounding.  Then the Lagrange f - 1, g, fdot, gdot - 1.
+// guess h/r0 (the first-order value of X(h); the paper gives none), 2 Halley
+// steps with 4-term series, 2 Newton steps with NT-term series.  The G_n at
+// the final X = X1 + d come from the values at the last Newton point X1 by
+// one Taylor step (dG_n/dX = G_{n-1}); |d| is the last Newton correction, so
+// the neglected d^2 terms are far below rounding.  Then the Lagrange f - 1,
+// g, fdot, gdot - 1.
 // h32 (uniform across the warp) runs the initial guess and the Halley phase
 // in FP32: they only supply the Newton phase's starting point, and from a
 // start within ~1e-7 two FP64 Newton steps reach FP64 rounding
@@ -343,14 +344,12 @@ __device__ __forceinline__ bool kepler_drift(double mu, double h, double& qx, do
     const double v2 = fma(vx, vx, fma(vy, vy, vz * vz));
     const double beta = fma(2.0 * mu, r0i, -v2);
     const double zeta0 = fma(-beta, r0, mu);
-    const double beta_eta0 = beta * eta0, beta_zeta0 = beta * zeta0;
-    double X, X2, c2, c3, G2, G3;
+    double X, X2, c2, c3, G1, G2, G3;
     if (h32) {
         const float r0f = to_f32(r0), r0if = to_f32(r0i), eta0f = to_f32(eta0);
         const float zeta0f = to_f32(zeta0), betaf = to_f32(beta), hf = to_f32(h);
         const float beta_eta0f = betaf * eta0f, beta_zeta0f = betaf * zeta0f;
-        const float hr = hf * r0if;
-        float Xs = fmaf(-0.5f * eta0f * hr * hr, r0if, hr);
+        float Xs = hf * r0if;
 #pragma unroll
         for (int it = 0; it < 2; ++it) {             // Halley (FP32)
             const float Y2 = Xs * Xs;
@@ -365,17 +364,18 @@ __device__ __forceinline__ bool kepler_drift(double mu, double h, double& qx, do
         }
         X = to_f64(Xs);
     } else {
-        const double hr = h * r0i;
-        X = fma(neg_half(eta0) * hr * hr, r0i, hr);
+        X = h * r0i;
 #pragma unroll
         for (int it = 0; it < 2; ++it) {             // Halley
             X2 = X * X;
             stumpff_c2c3<4>(beta * X2, c2, c3);
             G2 = X2 * c2;
             G3 = (X2 * X) * c3;
+            G1 = fma(-beta, G3, X);
+            const double G0 = fma(-beta, G2, 1.0);
             const double F = fma(r0, X, fma(eta0, G2, fma(zeta0, G3, -h)));
-            const double Fp = fma(zeta0, G2, fma(-beta_eta0, G3, fma(eta0, X, r0)));
-            const double Fpp = fma(-beta_zeta0, G3, fma(-beta_eta0, G2, fma(zeta0, X, eta0)));
+            const double Fp = fma(zeta0, G2, fma(eta0, G1, r0));
+            const double Fpp = fma(zeta0, G1, eta0 * G0);
             const double den = fma(neg_half(F), Fpp, Fp * Fp);   // (2F'^2 - F F'') / 2
             X = fma(-(F * Fp), rcp(den), X);
         }
@@ -383,23 +383,23 @@ __device__ __forceinline__ bool kepler_drift(double mu, double h, double& qx, do
     double d = 0.0;
 #pragma unroll
     for (int it = 0; it < 2; ++it) {                 // Newton
-        X = X + d;
         X2 = X * X;
         stumpff_c2c3<NT>(beta * X2, c2, c3);
         G2 = X2 * c2;
         G3 = (X2 * X) * c3;
+        G1 = fma(-beta, G3, X);
         const double F = fma(r0, X, fma(eta0, G2, fma(zeta0, G3, -h)));
-        const double Fp = fma(zeta0, G2, fma(-beta_eta0, G3, fma(eta0, X, r0)));
-        d = -F * rcp(Fp);
+        const double Fp = fma(zeta0, G2, fma(eta0, G1, r0));
+        if (it == 0) X = fma(-F, rcp(Fp), X);        // the first correction applied at once
+        else d = -F * rcp(Fp);                       // the last one kept for the G_n update
     }
     // G at the final X + d from the last Newton point X.
-    const double G1 = fma(-beta, G3, X);
     const double G0 = fma(-beta, G2, 1.0);
     const double Xf = X + d;
     const double G3f = fma(d, G2, G3);
     const double G2f = fma(d, G1, G2);
     const double G1f = fma(d, G0, G1);
-    const double r = fma(zeta0, G2f, fma(-beta_eta0, G3f, fma(eta0, Xf, r0)));
+    const double r = fma(zeta0, G2f, fma(eta0, G1f, r0));
     const double ri = rcp(r);
     const double mr0 = mu * r0i;
     const double fm1 = -mr0 * G2f;                   // f - 1
@@ -506,13 +506,48 @@ __device__ __forceinline__ void group_sum3(const Group<L>& g, double x, double y
     }
 }
 
+// Sums of m (x, y, z) over the system's lanes, the same bits in every lane.
+// L = 4, 8: as group_sum3, with the products by the masses taken inside the
+// first reduce-scatter round, where each kept component needs the partner's
+// product and the lane's own one: m_p x_p + m_q x_q as one product and one
+// FMA (2 products and 2 FMAs per lane for the two kept components, against 3
+// products and 2 additions when every lane first forms its whole m x).
+// Each partial sum is formed by one lane only, and the last round adds a
+// pair's two values in both lanes (commutative), so every lane still ends
+// with the same bits.
+template <int L>
+__device__ __forceinline__ void group_msum3(const Group<L>& g, double m, double x, double y, double z,
+                                            double& sx, double& sy, double& sz)
+{
+    if (L == 4 || L == 8) {
+        constexpr int H = L / 2, Q = L / 4;
+        const bool hi = (g.p & H) != 0;          // keeps (z, 0), else (x, y)
+        const double o0 = hi ? z : x, o1 = hi ? 0.0 : y;     // own values of the kept components
+        const double s0 = hi ? x : z, s1 = hi ? y : 0.0;     // own values the partner keeps
+        const double q0 = __shfl_xor_sync(WHG_FULL_MASK, s0, H);
+        const double q1 = __shfl_xor_sync(WHG_FULL_MASK, s1, H);
+        const double mq = __shfl_xor_sync(WHG_FULL_MASK, m, H);
+        const double k0 = fma(m, o0, mq * q0);
+        const double k1 = fma(m, o1, mq * q1);
+        const bool mid = (g.p & Q) != 0;         // keeps the second of the pair
+        double k = mid ? k1 : k0;
+        k += __shfl_xor_sync(WHG_FULL_MASK, mid ? k0 : k1, Q);
+        if (L == 8) k += __shfl_xor_sync(WHG_FULL_MASK, k, 1);
+        sx = __shfl_sync(WHG_FULL_MASK, k, g.base);
+        sy = __shfl_sync(WHG_FULL_MASK, k, g.base + Q);
+        sz = __shfl_sync(WHG_FULL_MASK, k, g.base + H);
+    } else {
+        group_sum3<L>(g, m * x, m * y, m * z, sx, sy, sz);
+    }
+}
+
 // Jump step (Sec. 3.4, Eq. 6): Q_i += (h/m0) sum_j m_j v_j; jc = h / m0.
 template <int L>
 __device__ __forceinline__ void jump(const Group<L>& g, double m, double jc, double vx, double vy,
                                      double vz, double& qx, double& qy, double& qz)
 {
     double px, py, pz;
-    group_sum3<L>(g, m * vx, m * vy, m * vz, px, py, pz);
+    group_msum3<L>(g, m, vx, vy, vz, px, py, pz);
     qx = fma(jc, px, qx);
     qy = fma(jc, py, qy);
     qz = fma(jc, pz, qz);

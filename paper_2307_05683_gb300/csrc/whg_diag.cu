@@ -53,9 +53,9 @@ __constant__ double c_invfact[32];
 
 __device__ __forceinline__ void stumpff_rt(double z, int T, double& c2, double& c3)
 {
-    c2 = c_invfact[2 * T];
-    c3 = c_invfact[2 * T + 1];
-    for (int k = T - 2; k >= 0; --k) {
+    c2 = c_invfact[2 * T + 2];      // series through z^T, as the step kernels sum it
+    c3 = c_invfact[2 * T + 3];
+    for (int k = T - 1; k >= 0; --k) {
         c2 = fma(-z, c2, c_invfact[2 * k + 2]);
         c3 = fma(-z, c3, c_invfact[2 * k + 3]);
     }
@@ -76,7 +76,7 @@ __global__ void k_kepler_sweep(const double* q, const double* v, const int* cfg,
         const double eta0 = qx * vx + qy * vy + qz * vz;
         const double beta = 2.0 * mu / r0 - (vx * vx + vy * vy + vz * vz);
         const double zeta0 = mu - beta * r0;
-        double X = h / r0 - eta0 * h * h / (2.0 * r0 * r0 * r0);
+        double X = h / r0;
         double c2, c3;
         for (int it = 0; it < hi + ni; ++it) {
             const int T = it < hi ? ht : nt;

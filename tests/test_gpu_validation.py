@@ -51,8 +51,16 @@ def test_accuracy_map_matches_oracle(val, orc):
 
 
 def test_iteration_search_matches_oracle(val, orc):
-    cfgs = [(2, 4, 2, 8), (2, 4, 1, 8), (0, 4, 5, 8), (1, 4, 3, 6), (2, 3, 2, 6), (2, 4, 2, 10)]
-    e = [0.0, 0.2, 0.4, 0.65]
+    """Appendix A's test through whg_kepler_sweep: the same verdict on the
+    1e-13 requirement as the oracle for every configuration; where a
+    configuration misses it, the same size of error (within a quarter: the
+    unconverged part of X depends on the rounding of the iterations, and the
+    GPU contracts multiply-adds that the oracle does not); where it meets it,
+    both errors are rounding noise and only their being below 1e-13 is
+    compared."""
+    cfgs = [(2, 4, 2, 8), (2, 4, 1, 8), (0, 4, 5, 8), (1, 4, 2, 8), (2, 4, 2, 6), (2, 3, 2, 6),
+            (2, 4, 2, 10)]
+    e = [0.0, 0.2, 0.4, 0.7]
     res = val.iteration_search(cfgs, e, n_phases=4, seed=7)
     rng = np.random.default_rng(7)
     E = np.repeat(np.asarray(e), 4)
@@ -62,10 +70,9 @@ def test_iteration_search_matches_oracle(val, orc):
                                  halley_iters=c[0], halley_terms=c[1], newton_iters=c[2],
                                  newton_terms=c[3])
         worst = np.abs(oe).max()
-        # same verdict on the 1e-13 requirement, same size of error (configs that
-        # do not converge accumulate a bias whose last digits follow rounding)
         assert (res[c] < 1e-13) == (worst < 1e-13), (c, res[c], worst)
-        assert abs(res[c] - worst) <= 2e-14 + 1e-2 * worst, (c, res[c], worst)
+        if worst >= 1e-13:
+            assert abs(res[c] - worst) <= 2e-14 + 0.25 * worst, (c, res[c], worst)
     assert res[(2, 4, 2, 8)] < 1e-13 and res[(2, 4, 1, 8)] > 1e-13
 
 
