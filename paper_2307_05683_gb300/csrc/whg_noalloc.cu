@@ -9,7 +9,6 @@
 // inputs and outputs; the working state (democratic heliocentric coordinates
 // between the init, step and read kernels) lives in the fixed array below.
 #include <cstdio>
-#include <mutex>
 
 #include "whg_internal.h"
 
@@ -30,10 +29,6 @@ static __device__ __align__(256) unsigned char g_scratch[kBytes];
 static __device__ unsigned g_noalloc_bounds;      // index-check flag of the debug build
 #endif
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-void* g_scratch_addr[kMaxDevices] = {};
-
 int noalloc_fail(int code, const char* fmt, const char* detail)
 {
     char msg[256];
@@ -42,22 +37,18 @@ int noalloc_fail(int code, const char* fmt, const char* detail)
     return code;
 }
 
-// Device address of g_scratch on the current device, looked up once per device.
+// Device address of g_scratch on the current device.  Looked up on every
+// call (the lookup allocates nothing), so that no address outlives a reset
+// of the device's primary context; the first lookup on a device may load the
+// library's device image, which is why the first call must precede any
+// stream capture.
 int scratch_address(void** out)
 {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return noalloc_fail(WHG_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(WHG_EINVAL, "device index %s not supported", "out of range");
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess || !p)
-            return noalloc_fail(WHG_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p)
+        return noalloc_fail(WHG_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+    *out = p;
     return WHG_OK;
 }
 
@@ -179,4 +170,22 @@ extern "C" int whg_integrate_noalloc(int n_systems, int max_planets, const whg_o
     e = whg_launch_read(st, bk, o, opt.newton_terms, l);
     if (e != cudaSuccess) return noalloc_fail(WHG_ECUDA, "read kernel: %s", cudaGetErrorString(e));
     return WHG_OK;
+}
+
+// Index-check flags of whg_integrate_noalloc in the debug build (see the
+// declaration in whg.h).  No allocation: the flag word is a device symbol.
+extern "C" int whg_noalloc_debug_bounds(unsigned* flag)
+{
+    if (!flag) return WHG_EINVAL;
+#ifdef WHG_DEBUG_BOUNDS
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(flag, g_noalloc_bounds, sizeof(unsigned));
+    const unsigned zero = 0;
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_noalloc_bounds, &zero, sizeof(unsigned));
+    if (e != cudaSuccess) return noalloc_fail(WHG_ECUDA, "whg_noalloc_debug_bounds: %s", cudaGetErrorString(e));
+    return WHG_OK;
+#else
+    *flag = 0;
+    return noalloc_fail(WHG_EINVAL, "whg_noalloc_debug_bounds: %s", "index checks are not compiled in (build with debug=True)");
+#endif
 }

@@ -83,6 +83,7 @@ def load():
                                                     ctypes.POINTER(ctypes.c_float)]),
             "whg_test_queue_timeout": (ctypes.c_int, [P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)]),
             "whg_debug_bounds": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_uint)]),
+            "whg_noalloc_debug_bounds": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint)]),
             "whg_kepler_sweep": (ctypes.c_int, [D, D, I, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                                 ctypes.c_longlong, D, D]),
             "whg_adjoint_forward": (ctypes.c_int, [P, ctypes.c_longlong, ctypes.c_int, D, D]),
@@ -107,7 +108,7 @@ def exported_symbols() -> list[str]:
             "whg_launch_count", "whg_last_error", "whg_destroy", "whg_measure_fp64_tflops",
             "whg_test_special", "whg_integrate_noalloc", "whg_adjoint_forward",
             "whg_adjoint_backward", "whg_kepler_sweep", "whg_probe_fp64_lanes", "whg_test_queue_timeout",
-            "whg_debug_bounds"]
+            "whg_debug_bounds", "whg_noalloc_debug_bounds"]
 
 
 def _check(ctx, rc: int) -> None:
@@ -281,6 +282,14 @@ def whg_debug_bounds(ctx) -> int:
     return int(flag.value)
 
 
+def whg_noalloc_debug_bounds() -> int:
+    """Index-check flag bits of whg_integrate_noalloc calls since the last
+    read (debug build only)."""
+    flag = ctypes.c_uint()
+    _check(None, load().whg_noalloc_debug_bounds(ctypes.byref(flag)))
+    return int(flag.value)
+
+
 def whg_test_queue_timeout(ctx, spin_limit: int) -> int:
     """Error flag (1 = a wait gave up) of the queue failure-path test (see whg.h)."""
     flag = ctypes.c_int()
@@ -319,7 +328,7 @@ class Integrator:
                  newton_terms: int = 8, lanes_per_system: int = 0, block_size: int = 0,
                  steps_per_launch: int = 0, close_encounter_hill: float = 0.0,
                  eject_factor: float = 0.0, graph_launches: int = 0, merge_jumps: bool = False,
-                 halley_fp32: bool = False, repack_frozen: bool = False, interaction_schedule: int = 0,
+                 halley_fp32: bool = False, repack_frozen: bool | None = None, interaction_schedule: int = 0,
                  queue_steps: int = 100, stream=None):
         opt = whg_default_options()
         opt.gr_mode = gr_mode
@@ -334,7 +343,7 @@ class Integrator:
         opt.graph_launches = graph_launches
         opt.merge_jumps = int(merge_jumps)
         opt.halley_fp32 = int(halley_fp32)
-        opt.repack_frozen = int(repack_frozen)
+        opt.repack_frozen = -1 if repack_frozen is None else int(bool(repack_frozen))   # None: auto
         opt.interaction_schedule = int(interaction_schedule)
         opt.queue_steps = int(queue_steps)
         self.S, self.N = int(n_systems), int(max_planets)

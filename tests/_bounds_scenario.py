@@ -48,4 +48,21 @@ whg.whg_adjoint_backward(it.ctx, None, gx, gu, gm)
 flags["device_init_adjoint"] = whg.whg_debug_bounds(it.ctx)
 it.close()
 
+# the allocation-free entry point: mixed planet counts with stop rules, then
+# systems of at most 3 planets, packed 8 per warp (4 lanes each by default)
+c = inputs.compact_ensemble(8, 200)
+small = inputs.Ensemble(c.masses[:, :4].copy(), c.pos[:, :4].copy(), c.vel[:, :4].copy(),
+                        np.minimum(c.n_planets, 3).astype(np.int32), c.dt.copy())
+for e, N, extra in ((ens, 8, dict(close_encounter_hill=6.0, eject_factor=3.0)), (small, 3, {})):
+    opt = whg.whg_default_options()
+    for k, v in extra.items():
+        setattr(opt, k, v)
+    S = e.n_systems
+    pos = torch.empty((S, 1 + N, 3), dtype=torch.float64, device="cuda")
+    whg.whg_integrate_noalloc(S, N, opt, dev(e.masses), dev(e.pos), dev(e.vel),
+                              dev(e.n_planets, torch.int32), dev(e.dt), 300, pos, torch.empty_like(pos),
+                              torch.empty(S, dtype=torch.int32, device="cuda"),
+                              torch.empty(S, dtype=torch.float64, device="cuda"))
+flags["noalloc_mixed_and_packed"] = whg.whg_noalloc_debug_bounds()
+
 print(json.dumps(flags))
