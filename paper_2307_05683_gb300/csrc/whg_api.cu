@@ -109,12 +109,14 @@ int warps_capacity(int S, int Nmax, int Lfixed)
 }
 
 // Bucket systems by lanes per system.  nplan may be null (all Nmax planets).
-// perm receives, for every internal system, the caller's index; returns
-// false (and fills nothing) when the layout is the identity.
+// perm receives, for every internal system, the caller's index (the
+// identity when every system gets the same lane group, which repacking
+// starts from); returns false when the layout is the identity.
 bool plan_layout(int S, int Nmax, int Lfixed, const int* nplan, WhgBuckets* bk, int* perm)
 {
     *bk = WhgBuckets{};
     if (Lfixed || !nplan) {
+        for (int s = 0; s < S; ++s) perm[s] = s;
         const int L = Lfixed ? Lfixed : whg_lanes_for_planets(Nmax);
         bk->nb = 1;
         bk->L[0] = L;
@@ -287,7 +289,7 @@ void whg_default_options(whg_options* opt)
     opt->graph_launches = 0;
     opt->merge_jumps = 0;
     opt->halley_fp32 = 0;
-    opt->repack_frozen = 0;
+    opt->repack_frozen = -1;
     opt->interaction_schedule = 0;
     opt->queue_steps = 100;
 }
@@ -323,8 +325,10 @@ int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options*
         return fail(nullptr, WHG_EINVAL, "steps_per_launch=%lld must be >= 0", opt.steps_per_launch);
     if (opt.graph_launches < 0 || opt.graph_launches > 4096)
         return fail(nullptr, WHG_EINVAL, "graph_launches=%d must be in 0..4096", opt.graph_launches);
-    if (opt.repack_frozen != 0 && opt.repack_frozen != 1)
-        return fail(nullptr, WHG_EINVAL, "repack_frozen=%d must be 0 or 1", opt.repack_frozen);
+    if (opt.repack_frozen < -1 || opt.repack_frozen > 1)
+        return fail(nullptr, WHG_EINVAL, "repack_frozen=%d must be -1, 0 or 1", opt.repack_frozen);
+    if (opt.repack_frozen < 0)                           // auto: on when a stop rule can stop systems
+        opt.repack_frozen = (opt.close_encounter_hill > 0.0 || opt.eject_factor > 0.0) ? 1 : 0;
     if (opt.interaction_schedule != 0 && opt.interaction_schedule != 1)
         return fail(nullptr, WHG_EINVAL, "interaction_schedule=%d must be 0 or 1", opt.interaction_schedule);
     if (opt.queue_steps < 0 || opt.queue_steps > 10000)

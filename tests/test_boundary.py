@@ -67,13 +67,14 @@ def test_options_struct_layout(lib_path):
     s.interaction_schedule = 4321
     s.queue_steps = 8765
     whg.load().whg_default_options(ctypes.byref(s))
-    assert s.halley_fp32 == 0 and s.repack_frozen == 0 and s.interaction_schedule == 0
+    assert s.halley_fp32 == 0 and s.repack_frozen == -1 and s.interaction_schedule == 0
     assert s.queue_steps == 100
 
 
 @pytest.mark.parametrize("field,value", [("gr_mode", 3), ("newton_terms", 7), ("lanes_per_system", 9),
                                          ("block_size", 48), ("steps_per_launch", -1),
                                          ("graph_launches", 5000), ("repack_frozen", 2),
+                                         ("repack_frozen", -2),
                                          ("interaction_schedule", 2), ("queue_steps", -1),
                                          ("queue_steps", 10001), ("close_encounter_hill", -1.0),
                                          ("eject_factor", float("inf"))])

@@ -85,15 +85,18 @@ def test_fp64_masked_lanes_cost_full_pipe_time():
     assert t32 > 0 and t8 >= 0.9 * t32, (t8, t32)
 
 
-@pytest.mark.parametrize("graphs", [0, 4])
-def test_repacking_stopped_systems_is_bitwise_neutral(whg, graphs):
+@pytest.mark.parametrize("graphs,lanes", [(0, 0), (4, 0), (0, 8)])
+def test_repacking_stopped_systems_is_bitwise_neutral(whg, graphs, lanes):
     """repack_frozen regroups running systems ahead of stopped ones inside
-    each planet-count bucket; every output (state, status, step counts,
-    energy, raw state) stays bit for bit the same, with and without graph
-    replay.  A tight close-encounter rule stops many systems on the way."""
+    each planet-count bucket (or the one lane group, lanes_per_system = 8);
+    every output (state, status, step counts, energy, raw state) stays bit
+    for bit the same, with and without graph replay.  A tight close-encounter
+    rule stops many systems on the way."""
     ens = inputs.compact_ensemble(45, 700)
-    kw = dict(close_encounter_hill=8.0, eject_factor=3.0, steps_per_launch=25, graph_launches=graphs)
-    plain = _run(whg, ens, 1500, **kw)
+    kw = dict(close_encounter_hill=8.0, eject_factor=3.0, steps_per_launch=25, graph_launches=graphs,
+              lanes_per_system=lanes)
+    plain = _run(whg, ens, 1500, repack_frozen=False, **kw)
+    auto = _run(whg, ens, 1500, **kw)                 # default: on, since a stop rule is on
     it = whg.Integrator(ens.n_systems, 8, repack_frozen=True, **kw)
     it.init(ens)
     for n in (700, 800):                              # two calls: the repack state carries over
@@ -111,6 +114,12 @@ def test_repacking_stopped_systems_is_bitwise_neutral(whg, graphs):
     assert np.array_equal(ref.energy(), E, equal_nan=True)
     ref.close()
     assert rep[-1] > plain[-1]                        # the repack kernels are counted
+    assert auto[-1] == rep[-1]
+    for a, b in zip(auto[:-1], rep[:-1]):
+        assert np.array_equal(a, b)
+    # without a stop rule the default does not repack: the same launches as off
+    assert _run(whg, ens, 600, steps_per_launch=25)[-1] == _run(whg, ens, 600, steps_per_launch=25,
+                                                                 repack_frozen=False)[-1]
 
 
 @pytest.mark.parametrize("extra", [{}, {"graph_launches": 4, "steps_per_launch": 250},
