@@ -36,7 +36,17 @@ def _key(ens, gr_mode: int, newton_terms: int, device: str) -> str:
     return f"{device}|S={ens.n_systems}|N={ens.max_planets}|hist={hist}|gr={gr_mode}|nt={newton_terms}"
 
 
-def candidates(ens):
+def candidates(ens, space: str = "full"):
+    """Configurations to time.  space "full": every dimension above.
+    space "launch": only the dimensions that leave results bit for bit
+    unchanged (block size, work queue, and short launches replayed as CUDA
+    graphs against automatic launch lengths), with the default packing and
+    interaction schedule."""
+    if space == "launch":
+        yield from ({"block_size": b, "queue_steps": q, "steps_per_launch": 0, "graph_launches": 0}
+                    for b, q in ((32, 100), (32, 0), (64, 0)))
+        yield {"block_size": 32, "queue_steps": 0, "steps_per_launch": 100, "graph_launches": 16}
+        return
     nmax = ens.max_planets
     uniform = 1
     while uniform < nmax:
@@ -50,6 +60,15 @@ def candidates(ens):
                "interaction_schedule": sched, "queue_steps": queue}
 
 
+def min_steps(ens, cfg: dict, window_s: float) -> int:
+    """Steps timed for one configuration: about window_s of work at ~2e8
+    system-steps/s, and at least two whole graph replays when graphs are on."""
+    n = max(16, int(2.0e8 * window_s / ens.n_systems))
+    if cfg.get("steps_per_launch"):
+        n = max(n, 2 * cfg["steps_per_launch"] * max(1, cfg.get("graph_launches", 0)))
+    return n
+
+
 def time_config(ens, cfg: dict, gr_mode: int, newton_terms: int, window_s: float = 0.05) -> float:
     """system-steps/s of one configuration over a window of about window_s."""
     import torch
@@ -59,9 +78,7 @@ def time_config(ens, cfg: dict, gr_mode: int, newton_terms: int, window_s: float
                         stream=stream.cuda_stream, **cfg)
     try:
         it.init(ens)
-        n = max(16, int(2.0e8 * window_s / S))
-        if cfg.get("steps_per_launch"):
-            n = max(n, 2 * cfg["steps_per_launch"] * max(1, cfg.get("graph_launches", 0)))
+        n = min_steps(ens, cfg, window_s)
         it.step(n)
         it.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -76,12 +93,15 @@ def time_config(ens, cfg: dict, gr_mode: int, newton_terms: int, window_s: float
 
 
 def tune(ens, gr_mode: int = 1, newton_terms: int = 8, cache_path: str | None = DEFAULT_CACHE,
-         window_s: float = 0.05, force: bool = False) -> dict:
+         window_s: float = 0.05, force: bool = False, space: str = "full") -> dict:
     """Best configuration for this ensemble shape (from the cache if present).
-    Returns the option values plus the measured rate under "system_steps_per_s"."""
+    Returns the option values plus the measured rate under "system_steps_per_s".
+    Candidates whose shortest timing (two graph replays) would exceed 20
+    windows of work are skipped: at that size a launch is long enough that
+    replaying it as a graph saves nothing."""
     import torch
     device = torch.cuda.get_device_name()
-    key = _key(ens, gr_mode, newton_terms, device)
+    key = _key(ens, gr_mode, newton_terms, device) + ("" if space == "full" else f"|space={space}")
     cache = {}
     if cache_path and os.path.exists(cache_path):
         try:
@@ -91,7 +111,10 @@ def tune(ens, gr_mode: int = 1, newton_terms: int = 8, cache_path: str | None = 
     if not force and key in cache:
         return dict(cache[key])
     results = []
-    for cfg in candidates(ens):
+    budget = 20 * max(16, int(2.0e8 * window_s / ens.n_systems))
+    for cfg in candidates(ens, space):
+        if min_steps(ens, cfg, window_s) > budget:
+            continue
         results.append((time_config(ens, cfg, gr_mode, newton_terms, window_s), cfg))
     rate, best = max(results, key=lambda r: r[0])
     entry = dict(best, system_steps_per_s=rate, tried=len(results), when=time.strftime("%Y-%m-%dT%H:%M:%S"))
@@ -109,5 +132,5 @@ def integrator(ens, gr_mode: int = 1, newton_terms: int = 8, **kw) -> "whg.Integ
     """An Integrator with the tuned launch configuration for this ensemble."""
     best = tune(ens, gr_mode, newton_terms, **kw)
     cfg = {k: best[k] for k in ("lanes_per_system", "block_size", "steps_per_launch", "graph_launches",
-                                "interaction_schedule", "queue_steps")}
+                                "interaction_schedule", "queue_steps") if k in best}
     return whg.Integrator(ens.n_systems, ens.max_planets, gr_mode=gr_mode, newton_terms=newton_terms, **cfg)

@@ -72,6 +72,28 @@ def test_tune_picks_fastest_and_caches(tmp_path, monkeypatch):
     assert len(calls) == n and json.load(open(path))
 
 
+def test_launch_space_is_results_neutral_and_skips_long_graph_timings(tmp_path, monkeypatch):
+    """space="launch" (the size sweep's tuning) tries only block size, work
+    queue and graph replay of short launches -- dimensions that leave results
+    bit for bit unchanged -- and skips the graph candidate once two replays
+    would take more than 20 timing windows (large ensembles)."""
+    import torch
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda *a: "stub")
+    cands = list(autotune.candidates(inputs.solar_ensemble(0, 8), "launch"))
+    assert all(set(c) == {"block_size", "queue_steps", "steps_per_launch", "graph_launches"} for c in cands)
+    assert any(c["graph_launches"] for c in cands) and all(c["block_size"] == 32 for c in cands
+                                                          if c["queue_steps"])
+    timed = []
+    monkeypatch.setattr(autotune, "time_config",
+                        lambda ens, cfg, g, nt, window_s=0.05: timed.append(cfg) or 1.0 + cfg["graph_launches"])
+    base = inputs.solar_ensemble(0, 16)
+    small = autotune.tune(base.tile(1 << 14), cache_path=None, space="launch")
+    assert small["graph_launches"] == 16 and small["tried"] == len(cands)
+    timed.clear()
+    large = autotune.tune(base.tile(1 << 18), cache_path=None, space="launch")
+    assert large["tried"] == len(cands) - 1 and not any(c["graph_launches"] for c in timed)
+
+
 def test_pericentre_timescale_eq4():
     """e = 0 gives the orbital period; the factor (1-e)^2/sqrt(1-e^2) shrinks
     it toward high eccentricity (Eq. 4)."""
