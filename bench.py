@@ -330,9 +330,10 @@ def measure_uneven(whg, torch, systems=1 << 16, steps=20000, seed=303):
     """Uneven batch: compact systems with 2..8 planets in one ensemble, both
     stop rules on (a pair closer than 1 mutual Hill radius, a planet beyond
     100x the largest initial a), 100-step launches replayed as CUDA graphs of
-    16, GR on.  Systems packed by planet count (n lanes each, 8 for n = 7)
-    against 8 lanes for every system, and packed with stopped systems
-    regrouped behind running ones after every graph replay (repack_frozen).
+    16, GR on.  Systems packed by planet count (n lanes each, 8 for n = 7;
+    the default, which with a stop rule on also regroups stopped systems
+    behind running ones after every graph replay), the same without that
+    regrouping (repack_frozen = 0), and 8 lanes for every system.
     Rates count every system for every
     step (a frozen system counts but costs nothing once its whole warp is
     frozen); CUDA events on the library's stream after a warm-up of 1600
@@ -341,7 +342,7 @@ def measure_uneven(whg, torch, systems=1 << 16, steps=20000, seed=303):
     stream = torch.cuda.Stream()
     out = {"workload": f"{systems} compact systems, 2..8 planets, stop rules on (1 mutual Hill radius, "
                        f"100 x largest initial a), GR on, 100-step launches in graphs of 16, {steps} steps"}
-    for name, lanes, repack in (("packed", 0, False), ("lanes8", 8, False), ("packed_repack", 0, True)):
+    for name, lanes, repack in (("packed", 0, None), ("packed_no_repack", 0, False), ("lanes8", 8, None)):
         it = whg.Integrator(systems, 8, gr_mode=1, lanes_per_system=lanes, steps_per_launch=100,
                             graph_launches=16, close_encounter_hill=1.0, eject_factor=100.0,
                             repack_frozen=repack, stream=stream.cuda_stream)

@@ -317,6 +317,17 @@ int whg_kepler_sweep(const double* q, const double* v, const int* cfg, int n, do
  * lanes cost full FP64 pipe time. */
 int whg_probe_fp64_lanes(int warps_per_sm, int active_lanes, int iters, float* ms);
 
+/* FP64 issue rate by instruction kind (no counterpart in the paper; it backs
+ * the choice of the roofline's denominator): warps_per_sm x (SM count)
+ * one-warp blocks, each lane running iters x 8 independent chains of one
+ * kind: 0 DFMA, 1 DMUL, 2 DADD, 3 DFMA plus one integer multiply-add per
+ * DFMA, 4 DFMA plus one FP32 FMA per DFMA.  *lanes_per_clk receives the FP64
+ * lane-operations per SM clock over the slowest block (clock64 around the
+ * loop, so independent of the clock frequency; all blocks are resident at
+ * once).  kind 0..4, warps_per_sm 1..32, iters 1..2^24; allocates and frees
+ * a small buffer; blocks. */
+int whg_probe_fp64_kind(int kind, int warps_per_sm, int iters, double* lanes_per_clk);
+
 /* Failure-path test of the work queue (no counterpart in the paper): one
  * queue launch on ctx (initialized, queue_steps > 0) whose unit counter starts
  * past every warp-group's first unit, so each unit waits for a predecessor

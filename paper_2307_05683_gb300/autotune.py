@@ -62,10 +62,15 @@ def candidates(ens, space: str = "full"):
 
 def min_steps(ens, cfg: dict, window_s: float) -> int:
     """Steps timed for one configuration: about window_s of work at ~2e8
-    system-steps/s, and at least two whole graph replays when graphs are on."""
+    system-steps/s, at least two whole graph replays when graphs are on, and
+    at least the 4 units per warp-group from which a launch uses the work
+    queue when the queue is on (else the timing would measure plain
+    launches)."""
     n = max(16, int(2.0e8 * window_s / ens.n_systems))
     if cfg.get("steps_per_launch"):
         n = max(n, 2 * cfg["steps_per_launch"] * max(1, cfg.get("graph_launches", 0)))
+    if cfg.get("queue_steps") and not cfg.get("steps_per_launch"):
+        n = max(n, 4 * cfg["queue_steps"])
     return n
 
 
@@ -96,9 +101,11 @@ def tune(ens, gr_mode: int = 1, newton_terms: int = 8, cache_path: str | None = 
          window_s: float = 0.05, force: bool = False, space: str = "full") -> dict:
     """Best configuration for this ensemble shape (from the cache if present).
     Returns the option values plus the measured rate under "system_steps_per_s".
-    Candidates whose shortest timing (two graph replays) would exceed 20
-    windows of work are skipped: at that size a launch is long enough that
-    replaying it as a graph saves nothing."""
+    Candidates whose shortest timing (two graph replays, or the work queue's
+    4 units) would exceed 20 windows of work are skipped: at that size one
+    launch is long enough that replaying it as a graph saves nothing, and
+    the warp-groups fill so many waves that the queue has little to
+    balance."""
     import torch
     device = torch.cuda.get_device_name()
     key = _key(ens, gr_mode, newton_terms, device) + ("" if space == "full" else f"|space={space}")

@@ -1,6 +1,7 @@
 // whg_diag.cu -- diagnostics of libwhg: FP64 pipe throughput and a test hook
 // for the library's own reciprocal / reciprocal square root.
 #include <cstdio>
+#include <vector>
 
 #include "whg_device.cuh"
 
@@ -43,6 +44,42 @@ __global__ void k_dfma_lanes(double* out, int iters, int active)
 #pragma unroll
     for (int j = 0; j < kChains; ++j) s += a[j];
     out[tid] = s;
+}
+
+// FP64 issue rate by instruction kind: 8 independent dependent chains per
+// thread of DFMA (KIND 0), DMUL (1) or DADD (2), or DFMA with one integer
+// multiply-add (3) or one FP32 FMA (4) on chains of their own after every
+// DFMA.  Each block records its SM cycles (clock64) around the loop.
+template <int KIND>
+__global__ void k_fp64_kind(double* out, long long* cycles, int iters)
+{
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    double a[kChains];
+    unsigned u[kChains];
+    float f[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) {
+        a[j] = 1.0 + 1e-3 * (double)(tid + j);
+        u[j] = 7u * (unsigned)tid + (unsigned)j;
+        f[j] = 1.0f + (float)j;
+    }
+    const long long t0 = clock64();
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < kChains; ++j) {
+            if (KIND == 1) a[j] = a[j] * 0.999999;
+            else if (KIND == 2) a[j] = a[j] + 1e-9;
+            else a[j] = fma(a[j], 0.999999, 1e-9);
+            if (KIND == 3) u[j] = u[j] * 3u + 1u;
+            if (KIND == 4) f[j] = fmaf(f[j], 0.999f, 1e-3f);
+        }
+    }
+    const long long t1 = clock64();
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) s += a[j] + (double)u[j] + (double)f[j];
+    out[tid] = s;
+    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
 // Kepler drift with runtime iteration counts and series lengths, for the
@@ -239,6 +276,45 @@ int whg_probe_fp64_lanes(int warps_per_sm, int active_lanes, int iters, float* m
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(out);
+    return rc;
+}
+
+int whg_probe_fp64_kind(int kind, int warps_per_sm, int iters, double* lanes_per_clk)
+{
+    if (!lanes_per_clk || kind < 0 || kind > 4 || warps_per_sm < 1 || warps_per_sm > 32 || iters < 1 ||
+        iters > (1 << 24))
+        return WHG_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return WHG_ECUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return WHG_ECUDA;
+    const int blocks = sms * warps_per_sm;        // one warp per block, at most 32 blocks per SM: all resident
+    void* buf = nullptr;
+    if (cudaMalloc(&buf, (sizeof(double) * 32 + sizeof(long long)) * (size_t)blocks) != cudaSuccess)
+        return WHG_ENOMEM;
+    double* out = (double*)buf;
+    long long* cyc = (long long*)(out + 32 * (size_t)blocks);
+    auto launch = [&](int n) {
+        switch (kind) {
+            case 0: k_fp64_kind<0><<<blocks, 32>>>(out, cyc, n); break;
+            case 1: k_fp64_kind<1><<<blocks, 32>>>(out, cyc, n); break;
+            case 2: k_fp64_kind<2><<<blocks, 32>>>(out, cyc, n); break;
+            case 3: k_fp64_kind<3><<<blocks, 32>>>(out, cyc, n); break;
+            default: k_fp64_kind<4><<<blocks, 32>>>(out, cyc, n); break;
+        }
+    };
+    launch(64);                                   // warm-up
+    launch(iters);
+    std::vector<long long> h((size_t)blocks);
+    int rc = WHG_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess ||
+        cudaMemcpy(h.data(), cyc, sizeof(long long) * h.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        rc = WHG_ECUDA;
+    } else {
+        long long mx = 1;
+        for (long long c : h) mx = c > mx ? c : mx;
+        *lanes_per_clk = (double)iters * kChains * 32.0 * warps_per_sm / (double)mx;
+    }
+    cudaFree(buf);
     return rc;
 }
 

@@ -82,6 +82,8 @@ def load():
             "whg_probe_fp64_lanes": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                     ctypes.POINTER(ctypes.c_float)]),
             "whg_test_queue_timeout": (ctypes.c_int, [P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)]),
+            "whg_probe_fp64_kind": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.POINTER(ctypes.c_double)]),
             "whg_debug_bounds": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_uint)]),
             "whg_noalloc_debug_bounds": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint)]),
             "whg_kepler_sweep": (ctypes.c_int, [D, D, I, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -108,7 +110,7 @@ def exported_symbols() -> list[str]:
             "whg_launch_count", "whg_last_error", "whg_destroy", "whg_measure_fp64_tflops",
             "whg_test_special", "whg_integrate_noalloc", "whg_adjoint_forward",
             "whg_adjoint_backward", "whg_kepler_sweep", "whg_probe_fp64_lanes", "whg_test_queue_timeout",
-            "whg_debug_bounds", "whg_noalloc_debug_bounds"]
+            "whg_debug_bounds", "whg_noalloc_debug_bounds", "whg_probe_fp64_kind"]
 
 
 def _check(ctx, rc: int) -> None:
@@ -273,6 +275,13 @@ def whg_probe_fp64_lanes(warps_per_sm: int, active_lanes: int, iters: int) -> fl
     _check(None, load().whg_probe_fp64_lanes(int(warps_per_sm), int(active_lanes), int(iters),
                                              ctypes.byref(ms)))
     return float(ms.value)
+
+
+def whg_probe_fp64_kind(kind: int, warps_per_sm: int, iters: int) -> float:
+    """FP64 lane-operations per SM clock of one instruction kind (see whg.h)."""
+    out = ctypes.c_double()
+    _check(None, load().whg_probe_fp64_kind(int(kind), int(warps_per_sm), int(iters), ctypes.byref(out)))
+    return float(out.value)
 
 
 def whg_debug_bounds(ctx) -> int:

@@ -85,6 +85,18 @@ def test_fp64_masked_lanes_cost_full_pipe_time():
     assert t32 > 0 and t8 >= 0.9 * t32, (t8, t32)
 
 
+def test_fp64_issue_rate_is_the_same_for_every_instruction_kind():
+    """A stream of DFMA, DMUL or DADD, alone or interleaved with integer or
+    FP32 work, issues at the same number of FP64 lane-operations per SM clock
+    (about 1.68 on GB300, under the nominal 2): no kind of FP64 instruction
+    is cheaper, so the step kernel's cost is its FP64 instruction count."""
+    from paper_2307_05683_gb300 import build, whg
+    build.build()
+    rates = [whg.whg_probe_fp64_kind(k, 8, 4000) for k in range(5)]
+    assert all(1.0 < r <= 2.05 for r in rates), rates
+    assert max(rates) <= 1.05 * min(rates), rates
+
+
 @pytest.mark.parametrize("graphs,lanes", [(0, 0), (4, 0), (0, 8)])
 def test_repacking_stopped_systems_is_bitwise_neutral(whg, graphs, lanes):
     """repack_frozen regroups running systems ahead of stopped ones inside

@@ -92,6 +92,9 @@ def test_launch_space_is_results_neutral_and_skips_long_graph_timings(tmp_path, 
     timed.clear()
     large = autotune.tune(base.tile(1 << 18), cache_path=None, space="launch")
     assert large["tried"] == len(cands) - 1 and not any(c["graph_launches"] for c in timed)
+    # a queue candidate is timed over at least 4 units, where launches use the queue
+    queued = [c for c in cands if c["queue_steps"]][0]
+    assert autotune.min_steps(base.tile(1 << 18), queued, 0.05) >= 4 * queued["queue_steps"]
 
 
 def test_pericentre_timescale_eq4():
