@@ -5,11 +5,14 @@
 // inertial positions, velocities and masses.  The forward run keeps the state
 // every K steps (checkpoints); the backward walks the segments in reverse:
 // each segment's K steps are recomputed from its checkpoint while a per-step
-// tape is written (drift input Q0, v0, final universal variable X, v after the
-// drift, Q during the kick, v after the kick), then the vector-Jacobian
-// products of J, I (+GR), J and K are applied step by step in reverse.  The
-// tape of segment s-1 is recomputed (second stream, second tape buffer) while
-// the products of segment s run.
+// tape is written, then the vector-Jacobian products of J, I (+GR), J and K
+// are applied step by step in reverse.  The tape holds, besides the state the
+// products need, every part of them that does not depend on the adjoints
+// (pair separations and powers of 1/r, the GR factors, the Kepler drift's
+// coefficients), so that the back kernels, which run one after another and
+// form the critical path, do only the work linear in the adjoints.  The tapes
+// of segments s-1 and s-2 are recomputed on two side streams (three tape
+// buffers) while the products of segment s run.
 //
 // VJPs, with lambda the adjoint of each quantity:
 //   J:  Q_i += c sum_j m_j v_j (c = (dt/2)/m0): lambda_v_j += c m_j Lambda,
@@ -49,80 +52,155 @@ __device__ __forceinline__ double stumpff_c(double z)
 }
 
 // Adjoint of one Kepler drift (Q0, v0) -> (Q1, v1) for time h, mu = G m0,
-// final universal variable X.  In: lq, lv = adjoints of Q1, v1.  Out: lq, lv
-// = adjoints of Q0, v0; lmu accumulates the adjoint of mu.
+// final universal variable X, split into the part that depends only on the
+// state (KeplerCoef, computed by the tape kernel off the critical path) and
+// the part linear in the adjoints (kepler_vjp_apply, run by the back kernel).
 //
 // c4, c5 come from their NT-term series and c2 = 1/2 - z c4, c3 = 1/6 - z c5
 // from the recurrence: the same series through z^NT that the forward drift
-// sums.  Every
-// Lagrange coefficient is mu times a function of the G_n, so the adjoints of
-// mu, r, r0 and G_n are written with f - 1, fdot and gdot - 1 themselves:
+// sums.  Every Lagrange coefficient is mu times a function of the G_n, so the
+// adjoints of mu, r, r0 and G_n are written with f - 1, fdot and gdot - 1
+// themselves:
 //   mub  = ((f-1) fb + fdot fdb + (gdot-1) gdb) / mu - G3 gb,
 //   rb   = -((fdot fdb + (gdot-1) gdb) / r,   r0b = -((f-1) fb + fdot fdb) / r0,
 //   G1b  = -(mu / (r r0)) fdb,  G2b = -(mu / r0) fb - (mu / r) gdb,  G3b = -mu gb,
 // with fb = lq.Q0, gb = lq.v0, fdb = lv.Q0, gdb = lv.v0.
+struct KeplerCoef {
+    double f, fd, g, gd, fm1, gdm1;      // Lagrange coefficients (and f - 1, gdot - 1)
+    double G0, G1, G2, G3;               // Stiefel functions at the final X
+    double ri, r0i, r0, eta0;            // 1/r, 1/r0, r0, Q0.v0
+    double A, B, C, Ar0i;                // mu/r0, mu/r, mu/(r r0), mu/r0^2
+    double bG1;                          // beta G1
+    double dG0, dG1, dG2, dG3;           // dG_n/dbeta
+    double dF;                           // dF/dbeta = r0 dG1 + eta0 dG2 + mu dG3
+};
+constexpr int kKeplerCoefs = 24;
+
 template <int NT>
-__device__ __forceinline__ void kepler_vjp(double mu, double muinv, double h, double qx, double qy,
-                                           double qz, double vx, double vy, double vz, double X,
-                                           double& lqx, double& lqy, double& lqz, double& lvx,
-                                           double& lvy, double& lvz, double& lmu)
+__device__ __forceinline__ KeplerCoef kepler_vjp_coef(double mu, double h, double qx, double qy, double qz,
+                                                      double vx, double vy, double vz, double X)
 {
+    KeplerCoef k;
     const double r0sq = fma(qx, qx, fma(qy, qy, qz * qz));
-    const double r0i = rsqrt(r0sq);
-    const double r0 = r0sq * r0i;
-    const double eta0 = fma(qx, vx, fma(qy, vy, qz * vz));
+    k.r0i = rsqrt(r0sq);
+    k.r0 = r0sq * k.r0i;
+    k.eta0 = fma(qx, vx, fma(qy, vy, qz * vz));
     const double v2 = fma(vx, vx, fma(vy, vy, vz * vz));
-    const double beta = fma(2.0 * mu, r0i, -v2);
+    const double beta = fma(2.0 * mu, k.r0i, -v2);
     const double X2 = X * X, X4 = X2 * X2;
     const double z = beta * X2;
     const double c4 = stumpff_c<4, NT>(z), c5 = stumpff_c<5, NT>(z);
     const double c2 = fma(-z, c4, 0.5), c3 = fma(-z, c5, 1.0 / 6.0);
-    const double G2 = X2 * c2, G3 = (X2 * X) * c3, G4 = X4 * c4, G5 = (X4 * X) * c5;
-    const double G0 = fma(-beta, G2, 1.0), G1 = fma(-beta, G3, X);
-    const double r = fma(r0, G0, fma(eta0, G1, mu * G2));
-    const double ri = rcp(r);
-    const double A = mu * r0i, B = mu * ri, C = A * ri;
-    const double fm1 = -A * G2, g = fma(-mu, G3, h), fd = -C * G1, gdm1 = -B * G2;
+    k.G2 = X2 * c2;
+    k.G3 = (X2 * X) * c3;
+    const double G4 = X4 * c4, G5 = (X4 * X) * c5;
+    k.G0 = fma(-beta, k.G2, 1.0);
+    k.G1 = fma(-beta, k.G3, X);
+    const double r = fma(k.r0, k.G0, fma(k.eta0, k.G1, mu * k.G2));
+    k.ri = rcp(r);
+    k.A = mu * k.r0i;
+    k.B = mu * k.ri;
+    k.C = k.A * k.ri;
+    k.Ar0i = k.A * k.r0i;
+    k.fm1 = -k.A * k.G2;
+    k.g = fma(-mu, k.G3, h);
+    k.fd = -k.C * k.G1;
+    k.gdm1 = -k.B * k.G2;
+    k.f = 1.0 + k.fm1;
+    k.gd = 1.0 + k.gdm1;
+    k.bG1 = beta * k.G1;
+    // dG_n/dbeta = (n G_{n+2} - X G_{n+1}) / 2
+    const double hX = 0.5 * X;
+    k.dG0 = -hX * k.G1;
+    k.dG1 = fma(-hX, k.G2, 0.5 * k.G3);
+    k.dG2 = fma(-hX, k.G3, G4);
+    k.dG3 = fma(-hX, G4, 1.5 * G5);
+    k.dF = fma(k.r0, k.dG1, fma(k.eta0, k.dG2, mu * k.dG3));
+    return k;
+}
+
+// The same coefficients from the values the forward drift computed anyway
+// (prologue, G1..G3 at the final X, 1/r and the Lagrange coefficients): only
+// the c4, c5 series for dG_n/dbeta are added.
+template <int NT>
+__device__ __forceinline__ KeplerCoef kepler_vjp_coef(double mu, double X, const DriftVals& dv)
+{
+    KeplerCoef k;
+    k.r0i = dv.r0i;
+    k.r0 = dv.r0;
+    k.eta0 = dv.eta0;
+    const double beta = dv.beta;
+    k.G1 = dv.G1;
+    k.G2 = dv.G2;
+    k.G3 = dv.G3;
+    k.G0 = fma(-beta, k.G2, 1.0);
+    k.ri = dv.ri;
+    k.A = dv.A;
+    k.B = mu * k.ri;
+    k.C = k.A * k.ri;
+    k.Ar0i = k.A * k.r0i;
+    k.fm1 = dv.fm1;
+    k.g = dv.g;
+    k.fd = dv.fd;
+    k.gdm1 = dv.gdm1;
+    k.f = 1.0 + k.fm1;
+    k.gd = 1.0 + k.gdm1;
+    k.bG1 = beta * k.G1;
+    const double X2 = X * X, X4 = X2 * X2;
+    const double z = beta * X2;
+    const double G4 = X4 * stumpff_c<4, NT>(z), G5 = (X4 * X) * stumpff_c<5, NT>(z);
+    const double hX = 0.5 * X;
+    k.dG0 = -hX * k.G1;
+    k.dG1 = fma(-hX, k.G2, 0.5 * k.G3);
+    k.dG2 = fma(-hX, k.G3, G4);
+    k.dG3 = fma(-hX, G4, 1.5 * G5);
+    k.dF = fma(k.r0, k.dG1, fma(k.eta0, k.dG2, mu * k.dG3));
+    return k;
+}
+
+// In: lq, lv = adjoints of Q1, v1.  Out: lq, lv = adjoints of Q0, v0; lmu
+// accumulates the adjoint of mu.
+__device__ __forceinline__ void kepler_vjp_apply(const KeplerCoef& k, double mu, double muinv, double qx,
+                                                 double qy, double qz, double vx, double vy, double vz,
+                                                 double& lqx, double& lqy, double& lqz, double& lvx,
+                                                 double& lvy, double& lvz, double& lmu)
+{
     // (a) outputs Q1 = f Q0 + g v0, v1 = fd Q0 + gd v0
     const double fb = fma(lqx, qx, fma(lqy, qy, lqz * qz));
     const double gb = fma(lqx, vx, fma(lqy, vy, lqz * vz));
     const double fdb = fma(lvx, qx, fma(lvy, qy, lvz * qz));
     const double gdb = fma(lvx, vx, fma(lvy, vy, lvz * vz));
-    const double f = 1.0 + fm1, gd = 1.0 + gdm1;
-    double nqx = fma(f, lqx, fd * lvx), nqy = fma(f, lqy, fd * lvy), nqz = fma(f, lqz, fd * lvz);
-    double nvx = fma(g, lqx, gd * lvx), nvy = fma(g, lqy, gd * lvy), nvz = fma(g, lqz, gd * lvz);
+    double nqx = fma(k.f, lqx, k.fd * lvx), nqy = fma(k.f, lqy, k.fd * lvy), nqz = fma(k.f, lqz, k.fd * lvz);
+    double nvx = fma(k.g, lqx, k.gd * lvx), nvy = fma(k.g, lqy, k.gd * lvy), nvz = fma(k.g, lqz, k.gd * lvz);
     // (b) through f, g, fd, gd
-    const double tf = fm1 * fb, tfd = fd * fdb, tgd = gdm1 * gdb;
-    double mub = fma(tf + tfd + tgd, muinv, -G3 * gb);
-    const double rb = -(tfd + tgd) * ri;
-    double r0b = -(tf + tfd) * r0i;
-    double G1b = -C * fdb;
-    double G2b = fma(-A, fb, -B * gdb);
+    const double tf = k.fm1 * fb, tfd = k.fd * fdb, tgd = k.gdm1 * gdb;
+    double mub = fma(tf + tfd + tgd, muinv, -k.G3 * gb);
+    const double rb = -(tfd + tgd) * k.ri;
+    double r0b = -(tf + tfd) * k.r0i;
+    double G1b = -k.C * fdb;
+    double G2b = fma(-k.A, fb, -k.B * gdb);
     const double G3b = -mu * gb;
     // (c) r = r0 G0 + eta0 G1 + mu G2
-    r0b = fma(rb, G0, r0b);
-    double eta0b = rb * G1;
-    mub = fma(rb, G2, mub);
-    const double G0b = rb * r0;
-    G1b = fma(rb, eta0, G1b);
+    r0b = fma(rb, k.G0, r0b);
+    double eta0b = rb * k.G1;
+    mub = fma(rb, k.G2, mub);
+    const double G0b = rb * k.r0;
+    G1b = fma(rb, k.eta0, G1b);
     G2b = fma(rb, mu, G2b);
-    // (d) G_n(beta, X): dG_n/dX = G_{n-1}, dG_0/dX = -beta G1, dG_n/dbeta = (n G_{n+2} - X G_{n+1})/2
-    const double hX = 0.5 * X;
-    const double dG0 = -hX * G1, dG1 = fma(-hX, G2, 0.5 * G3);
-    const double dG2 = fma(-hX, G3, G4), dG3 = fma(-hX, G4, 1.5 * G5);
-    const double Xb = fma(-G0b * beta, G1, fma(G1b, G0, fma(G2b, G1, G3b * G2)));
-    double betab = fma(G0b, dG0, fma(G1b, dG1, fma(G2b, dG2, G3b * dG3)));
+    // (d) G_n(beta, X): dG_n/dX = G_{n-1}, dG_0/dX = -beta G1
+    const double Xb = fma(-G0b, k.bG1, fma(G1b, k.G0, fma(G2b, k.G1, G3b * k.G2)));
+    double betab = fma(G0b, k.dG0, fma(G1b, k.dG1, fma(G2b, k.dG2, G3b * k.dG3)));
     // (e) X implicit in F = r0 G1 + eta0 G2 + mu G3 - h = 0, dF/dX = r
-    const double w = Xb * ri;
-    r0b = fma(-w, G1, r0b);
-    eta0b = fma(-w, G2, eta0b);
-    mub = fma(-w, G3, mub);
-    betab = fma(-w, fma(r0, dG1, fma(eta0, dG2, mu * dG3)), betab);
+    const double w = Xb * k.ri;
+    r0b = fma(-w, k.G1, r0b);
+    eta0b = fma(-w, k.G2, eta0b);
+    mub = fma(-w, k.G3, mub);
+    betab = fma(-w, k.dF, betab);
     // (f) beta = 2 mu / r0 - v.v, eta0 = Q.v, r0 = |Q|
     const double b2 = 2.0 * betab;
-    mub = fma(b2, r0i, mub);
-    r0b = fma(-b2 * A, r0i, r0b);
-    const double rq = r0b * r0i;
+    mub = fma(b2, k.r0i, mub);
+    r0b = fma(-b2, k.Ar0i, r0b);
+    const double rq = r0b * k.r0i;
     nvx = fma(-b2, vx, fma(eta0b, qx, nvx));
     nvy = fma(-b2, vy, fma(eta0b, qy, nvy));
     nvz = fma(-b2, vz, fma(eta0b, qz, nvz));
@@ -134,100 +212,128 @@ __device__ __forceinline__ void kepler_vjp(double mu, double muinv, double h, do
     lmu += mub;
 }
 
+template <int NT>
+__device__ __forceinline__ void kepler_vjp(double mu, double muinv, double h, double qx, double qy,
+                                           double qz, double vx, double vy, double vz, double X,
+                                           double& lqx, double& lqy, double& lqz, double& lvx,
+                                           double& lvy, double& lvz, double& lmu)
+{
+    const KeplerCoef k = kepler_vjp_coef<NT>(mu, h, qx, qy, qz, vx, vy, vz, X);
+    kepler_vjp_apply(k, mu, muinv, qx, qy, qz, vx, vy, vz, lqx, lqy, lqz, lvx, lvy, lvz, lmu);
+}
+
 // Adjoint of a jump Q_i += c sum_j m_j v_j with the velocities (vx, vy, vz)
-// it used; lambda_Q passes through unchanged.
+// it used; lambda_Q passes through unchanged.  cmu = c / m0.
 template <int L>
-__device__ __forceinline__ void jump_vjp(const Group<L>& g, double m, double c, double mu, double vx,
+__device__ __forceinline__ void jump_vjp(const Group<L>& g, double m, double c, double cmu, double vx,
                                          double vy, double vz, double lqx, double lqy, double lqz,
                                          double& lvx, double& lvy, double& lvz, double& lm, double& lmu)
 {
     double Lx, Ly, Lz;
     group_sum3<L>(g, lqx, lqy, lqz, Lx, Ly, Lz);
-    lvx += c * m * Lx;
-    lvy += c * m * Ly;
-    lvz += c * m * Lz;
-    const double vd = vx * Lx + vy * Ly + vz * Lz;
-    lm += c * vd;
-    lmu -= (c / mu) * m * vd;
+    const double cm = c * m;
+    lvx = fma(cm, Lx, lvx);
+    lvy = fma(cm, Ly, lvy);
+    lvz = fma(cm, Lz, lvz);
+    const double vd = fma(vx, Lx, fma(vy, Ly, vz * Lz));
+    lm = fma(c, vd, lm);
+    lmu = fma(-cmu * m, vd, lmu);
 }
 
-// Adjoint of the interaction kick (+GR) at positions Q, with lambda_v the
-// adjoint of the velocities after it (which pass through unchanged).
+// Tape layout: per lane and step, WHG_TAPE_W doubles at stride NL.  Besides
+// the state the back kernel needs (velocities for the jumps, positions for
+// the GR term, the drift input), the tape holds everything of the kick and
+// drift VJPs that does not depend on the adjoints, computed by the tape
+// kernel: per pair round the separation d = Q_j - Q_i, r^-3, 3 r^-5 and
+// dt r^-3, the GR factors, and the Kepler coefficients.
+constexpr int kTV3 = 0;        // v after the kick (input of the second jump)
+constexpr int kTQ2 = 3;        // Q during the kick
+constexpr int kTRound = 6;     // 4 rounds x 8 pair factors (see KickTape), written by kick()
+constexpr int kTGR = 38;       // c = kgr/|Q|^4, 4 c/|Q|^2, 2 c/m0, written by kick()
+constexpr int kTV1 = 41;       // v after the drift (input of the first jump)
+constexpr int kTQ0 = 44;       // drift input Q0
+constexpr int kTV0 = 47;       // drift input v0
+constexpr int kTKC = 50;       // KeplerCoef
+static_assert(kTKC + kKeplerCoefs == WHG_TAPE_W, "tape layout");
+static_assert(kTGR == kTRound + 4 * kKickTapeRound, "kick() writes its GR factors after 4 rounds");
+
+// Adjoint of the interaction kick (+GR) from the tape, with lambda_v the
+// adjoint of the velocities after it (which pass through unchanged).  Per
+// pair (d = Q_j - Q_i, a = lambda_v_i.d, b = lambda_v_j.d):
+//   lambda_d = hm_j r^-3 lambda_v_i - hm_i r^-3 lambda_v_j - s d,
+//   s = 3 r^-5 (hm_j a - hm_i b), lambda_Q_j += lambda_d, lambda_Q_i -= lambda_d,
+//   lambda_m_i -= dt r^-3 b, lambda_m_j += dt r^-3 a.
 template <int L, int GRM>
-__device__ __forceinline__ void kick_vjp(const Group<L>& g, double qx, double qy, double qz, double m,
-                                         double hm, double dt, double mu, double kgr, double lvx,
-                                         double lvy, double lvz, double& lqx, double& lqy,
-                                         double& lqz, double& lm, double& lmu)
+__device__ __forceinline__ void kick_vjp(const Group<L>& g, const double* tp, size_t NL, double qx, double qy,
+                                         double qz, double m, double hm, double muinv, double lvx,
+                                         double lvy, double lvz, double& lqx, double& lqy, double& lqz,
+                                         double& lm, double& lmu)
 {
+    (void)hm;
 #pragma unroll
     for (int k = 1; 2 * k < L; ++k) {
         const int to = g.at(k), from = g.at(-k);
-        const double dx = __shfl_sync(WHG_FULL_MASK, qx, to) - qx;
-        const double dy = __shfl_sync(WHG_FULL_MASK, qy, to) - qy;
-        const double dz = __shfl_sync(WHG_FULL_MASK, qz, to) - qz;
-        const double hmj = __shfl_sync(WHG_FULL_MASK, hm, to);
+        const double* t = tp + (size_t)(kTRound + kKickTapeRound * (k - 1)) * NL;
+        const double dx = t[0], dy = t[NL], dz = t[2 * NL];
+        const double p3j = t[3 * NL], p3i = t[4 * NL], p5j = t[5 * NL], p5i = t[6 * NL], dtr3 = t[7 * NL];
         const double ljx = __shfl_sync(WHG_FULL_MASK, lvx, to);
         const double ljy = __shfl_sync(WHG_FULL_MASK, lvy, to);
         const double ljz = __shfl_sync(WHG_FULL_MASK, lvz, to);
-        const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-        const double r1i = rsqrt(r2);
-        const double r2i = r1i * r1i, r3i = r2i * r1i, r5i = r3i * r2i;
-        const double wx = hmj * lvx - hm * ljx, wy = hmj * lvy - hm * ljy, wz = hmj * lvz - hm * ljz;
-        const double s3 = 3.0 * (wx * dx + wy * dy + wz * dz) * r5i;
-        const double ldx = r3i * wx - s3 * dx, ldy = r3i * wy - s3 * dy, ldz = r3i * wz - s3 * dz;
+        const double a = fma(lvx, dx, fma(lvy, dy, lvz * dz));
+        const double b = fma(ljx, dx, fma(ljy, dy, ljz * dz));
+        const double sd = fma(p5j, a, -p5i * b);
+        const double ldx = fma(p3j, lvx, fma(-p3i, ljx, -sd * dx));
+        const double ldy = fma(p3j, lvy, fma(-p3i, ljy, -sd * dy));
+        const double ldz = fma(p3j, lvz, fma(-p3i, ljz, -sd * dz));
         lqx -= ldx;
         lqy -= ldy;
         lqz -= ldz;
-        lm -= dt * r3i * (ljx * dx + ljy * dy + ljz * dz);
-        const double lmj = dt * r3i * (lvx * dx + lvy * dy + lvz * dz);   // for the partner
+        lm = fma(-dtr3, b, lm);
+        const double lmj = dtr3 * a;                  // for the partner
         lqx += __shfl_sync(WHG_FULL_MASK, ldx, from);
         lqy += __shfl_sync(WHG_FULL_MASK, ldy, from);
         lqz += __shfl_sync(WHG_FULL_MASK, ldz, from);
         lm += __shfl_sync(WHG_FULL_MASK, lmj, from);
     }
-    if (L >= 2 && (L & 1) == 0) {
+    if (L >= 2 && (L & 1) == 0) {                     // both lanes of each pair evaluate it
         const int to = g.at(L / 2);
-        const double dx = __shfl_sync(WHG_FULL_MASK, qx, to) - qx;
-        const double dy = __shfl_sync(WHG_FULL_MASK, qy, to) - qy;
-        const double dz = __shfl_sync(WHG_FULL_MASK, qz, to) - qz;
-        const double hmj = __shfl_sync(WHG_FULL_MASK, hm, to);
-        const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-        const double r1i = rsqrt(r2);
-        const double r2i = r1i * r1i, r3i = r2i * r1i, r5i = r3i * r2i;
-        const double wx = hmj * lvx, wy = hmj * lvy, wz = hmj * lvz;
-        const double s3 = 3.0 * (wx * dx + wy * dy + wz * dz) * r5i;
-        const double ldx = r3i * wx - s3 * dx, ldy = r3i * wy - s3 * dy, ldz = r3i * wz - s3 * dz;
+        const double* t = tp + (size_t)(kTRound + kKickTapeRound * (L / 2 - 1)) * NL;
+        const double dx = t[0], dy = t[NL], dz = t[2 * NL];
+        const double p3j = t[3 * NL], p5j = t[5 * NL], dtr3 = t[7 * NL];
+        const double a = fma(lvx, dx, fma(lvy, dy, lvz * dz));
+        const double sd = p5j * a;
+        const double ldx = fma(p3j, lvx, -sd * dx);
+        const double ldy = fma(p3j, lvy, -sd * dy);
+        const double ldz = fma(p3j, lvz, -sd * dz);
         lqx -= ldx;
         lqy -= ldy;
         lqz -= ldz;
-        const double lmj = dt * r3i * (lvx * dx + lvy * dy + lvz * dz);
+        const double lmj = dtr3 * a;
         lqx += __shfl_sync(WHG_FULL_MASK, ldx, to);
         lqy += __shfl_sync(WHG_FULL_MASK, ldy, to);
         lqz += __shfl_sync(WHG_FULL_MASK, ldz, to);
         lm += __shfl_sync(WHG_FULL_MASK, lmj, to);
     }
     if (GRM != 0) {
-        const double r2 = fma(qx, qx, fma(qy, qy, qz * qz));
-        const double ri2 = rcp(r2);
-        const double c = kgr * (ri2 * ri2);
+        const double c = tp[kTGR * NL], c4r = tp[(kTGR + 1) * NL], c2mu = tp[(kTGR + 2) * NL];
         double ax = lvx, ay = lvy, az = lvz;             // adjoint of this planet's a_GR
         if (GRM == 2) {
             double Lx, Ly, Lz;
             group_sum3<L>(g, lvx, lvy, lvz, Lx, Ly, Lz);
-            const double aL = c * (qx * Lx + qy * Ly + qz * Lz);   // a_i . Lambda_v
-            lm -= aL / mu;
-            lmu += m * aL / (mu * mu);
-            const double mr = m / mu;
-            ax -= mr * Lx;
-            ay -= mr * Ly;
-            az -= mr * Lz;
+            const double aL = c * fma(qx, Lx, fma(qy, Ly, qz * Lz));   // a_i . Lambda_v
+            lm = fma(-aL, muinv, lm);
+            lmu = fma(m * aL, muinv * muinv, lmu);
+            const double mr = m * muinv;
+            ax = fma(-mr, Lx, ax);
+            ay = fma(-mr, Ly, ay);
+            az = fma(-mr, Lz, az);
         }
-        const double s = qx * ax + qy * ay + qz * az;
-        const double c4 = 4.0 * c * s * ri2;
-        lqx += c * ax - c4 * qx;
-        lqy += c * ay - c4 * qy;
-        lqz += c * az - c4 * qz;
-        lmu += 2.0 * (c / mu) * s;
+        const double s = fma(qx, ax, fma(qy, ay, qz * az));
+        const double c4 = c4r * s;
+        lqx += fma(c, ax, -c4 * qx);
+        lqy += fma(c, ay, -c4 * qy);
+        lqz += fma(c, az, -c4 * qz);
+        lmu = fma(c2mu, s, lmu);
     }
 }
 
@@ -299,9 +405,8 @@ __device__ __forceinline__ void loss_body(const WhgState& st, const WhgBuckets& 
     lam[7 * adj.NL + lane] = lmu;                    // lambda_m0 (partial, summed over lanes)
 }
 
-// Tape of one segment: its steps recomputed from the checkpoint, writing per
-// step the drift input (Q0, v0), the final X, v after the drift, Q during the
-// kick and v after the kick into tape buffer `buf`.
+// Tape of one segment: its steps recomputed from the checkpoint (bitwise the
+// forward's arithmetic), writing per step the tape fields listed above.
 template <int L, int NT, int GRM>
 __device__ __forceinline__ void tape_body(const WhgState& st, const WhgBuckets& bk, const WhgAdj& adj,
                                           int b, int w, int seg, long long s0, int nk, int buf)
@@ -324,19 +429,26 @@ __device__ __forceinline__ void tape_body(const WhgState& st, const WhgBuckets& 
     const double nothr[4] = {0.0, 0.0, 0.0, 0.0};
     double* tape = adj.tape + (size_t)buf * adj.tape_len;
     for (int k = 0; k < nk; ++k) {
-        double* tp = tape + (size_t)k * 16 * NL + lane;
-        tp[0 * NL] = qx; tp[1 * NL] = qy; tp[2 * NL] = qz;
-        tp[3 * NL] = vx; tp[4 * NL] = vy; tp[5 * NL] = vz;
+        double* tp = tape + (size_t)k * WHG_TAPE_W * NL + lane;
+        tp[kTQ0 * NL] = qx; tp[(kTQ0 + 1) * NL] = qy; tp[(kTQ0 + 2) * NL] = qz;
+        tp[kTV0 * NL] = vx; tp[(kTV0 + 1) * NL] = vy; tp[(kTV0 + 2) * NL] = vz;
         const double h = (s0 + k == 0) ? 0.5 * dt : dt;
         double X;
-        kepler_drift<NT>(mu, h, qx, qy, qz, vx, vy, vz, X, st.halley32 != 0);
-        tp[6 * NL] = X;
-        tp[7 * NL] = vx; tp[8 * NL] = vy; tp[9 * NL] = vz;
+        DriftVals dv;
+        kepler_drift<NT, true>(mu, h, qx, qy, qz, vx, vy, vz, X, st.halley32 != 0, &dv);
+        {
+            const KeplerCoef kc = kepler_vjp_coef<NT>(mu, X, dv);
+            const double* kv = reinterpret_cast<const double*>(&kc);
+#pragma unroll
+            for (int i = 0; i < kKeplerCoefs; ++i) tp[(kTKC + i) * NL] = kv[i];
+        }
+        tp[kTV1 * NL] = vx; tp[(kTV1 + 1) * NL] = vy; tp[(kTV1 + 2) * NL] = vz;
         const bool merged = GRM == 0 && st.merge;
         jump<L>(g, m, merged ? 2.0 * c : c, vx, vy, vz, qx, qy, qz);
-        tp[10 * NL] = qx; tp[11 * NL] = qy; tp[12 * NL] = qz;
-        kick<L, GRM>(g, qx, qy, qz, hm, mrat, kgr, nothr, vx, vy, vz, st.full_rotation != 0);
-        tp[13 * NL] = vx; tp[14 * NL] = vy; tp[15 * NL] = vz;
+        tp[kTQ2 * NL] = qx; tp[(kTQ2 + 1) * NL] = qy; tp[(kTQ2 + 2) * NL] = qz;
+        const KickTape kt{tp + (size_t)kTRound * NL, NL, dt, 2.0 / mu};
+        kick<L, GRM, true>(g, qx, qy, qz, hm, mrat, kgr, nothr, vx, vy, vz, st.full_rotation != 0, &kt);
+        tp[kTV3 * NL] = vx; tp[(kTV3 + 1) * NL] = vy; tp[(kTV3 + 2) * NL] = vz;
         if (!merged) jump<L>(g, m, c, vx, vy, vz, qx, qy, qz);
         if (!real) {                                  // lanes without a planet stay parked
             qx = pqx; qy = pqy; qz = pqz;
@@ -346,7 +458,9 @@ __device__ __forceinline__ void tape_body(const WhgState& st, const WhgBuckets& 
 }
 
 // Pull the adjoint back through the steps of one segment, last step first,
-// from tape buffer `buf`.
+// from tape buffer `buf`.  Only the work linear in the adjoints runs here:
+// the back kernels of consecutive segments form the critical path, while the
+// tape kernels run beside them.
 template <int L, int NT, int GRM>
 __device__ __forceinline__ void back_body(const WhgState& st, const WhgBuckets& bk, const WhgAdj& adj,
                                           int b, int w, long long s0, int nk, int buf)
@@ -360,27 +474,29 @@ __device__ __forceinline__ void back_body(const WhgState& st, const WhgBuckets& 
     const double mu = pl.has_sys ? st.m0[s] : 1.0;
     const double dt = pl.has_sys ? st.dt[s] : 1.0e-3;
     const bool real = pl.has_sys && g.p < st.nplan[s];
-    const double hm = dt * m, c = (0.5 * dt) / mu, muinv = 1.0 / mu;
-    const double kgr = GRM ? (-6.0 * mu * mu * dt) / (st.c_light * st.c_light) : 0.0;
+    const double hm = dt * m, c = (0.5 * dt) / mu, muinv = 1.0 / mu, cmu = c * muinv;
     const double* tape = adj.tape + (size_t)buf * adj.tape_len;
     double* lam = adj.lam;
     double lqx = lam[0 * NL + lane], lqy = lam[1 * NL + lane], lqz = lam[2 * NL + lane];
     double lvx = lam[3 * NL + lane], lvy = lam[4 * NL + lane], lvz = lam[5 * NL + lane];
     double lm = lam[6 * NL + lane], lmu = lam[7 * NL + lane];
     for (int k = nk - 1; k >= 0; --k) {
-        const double* tp = tape + (size_t)k * 16 * NL + lane;
-        const double q0x = tp[0 * NL], q0y = tp[1 * NL], q0z = tp[2 * NL];
-        const double v0x = tp[3 * NL], v0y = tp[4 * NL], v0z = tp[5 * NL];
-        const double X = tp[6 * NL];
-        const double v1x = tp[7 * NL], v1y = tp[8 * NL], v1z = tp[9 * NL];
-        const double q2x = tp[10 * NL], q2y = tp[11 * NL], q2z = tp[12 * NL];
-        const double v3x = tp[13 * NL], v3y = tp[14 * NL], v3z = tp[15 * NL];
-        const double h = (s0 + k == 0) ? 0.5 * dt : dt;
+        const double* tp = tape + (size_t)k * WHG_TAPE_W * NL + lane;
         const bool merged = GRM == 0 && st.merge;
-        if (!merged) jump_vjp<L>(g, m, c, mu, v3x, v3y, v3z, lqx, lqy, lqz, lvx, lvy, lvz, lm, lmu);
-        kick_vjp<L, GRM>(g, q2x, q2y, q2z, m, hm, dt, mu, kgr, lvx, lvy, lvz, lqx, lqy, lqz, lm, lmu);
-        jump_vjp<L>(g, m, merged ? 2.0 * c : c, mu, v1x, v1y, v1z, lqx, lqy, lqz, lvx, lvy, lvz, lm, lmu);
-        kepler_vjp<NT>(mu, muinv, h, q0x, q0y, q0z, v0x, v0y, v0z, X, lqx, lqy, lqz, lvx, lvy, lvz, lmu);
+        if (!merged)
+            jump_vjp<L>(g, m, c, cmu, tp[kTV3 * NL], tp[(kTV3 + 1) * NL], tp[(kTV3 + 2) * NL], lqx, lqy, lqz,
+                        lvx, lvy, lvz, lm, lmu);
+        kick_vjp<L, GRM>(g, tp, NL, tp[kTQ2 * NL], tp[(kTQ2 + 1) * NL], tp[(kTQ2 + 2) * NL], m, hm, muinv,
+                         lvx, lvy, lvz, lqx, lqy, lqz, lm, lmu);
+        const double cj = merged ? 2.0 * c : c;
+        jump_vjp<L>(g, m, cj, cj * muinv, tp[kTV1 * NL], tp[(kTV1 + 1) * NL], tp[(kTV1 + 2) * NL], lqx, lqy,
+                    lqz, lvx, lvy, lvz, lm, lmu);
+        KeplerCoef kc;
+        double* kv = reinterpret_cast<double*>(&kc);
+#pragma unroll
+        for (int i = 0; i < kKeplerCoefs; ++i) kv[i] = tp[(kTKC + i) * NL];
+        kepler_vjp_apply(kc, mu, muinv, tp[kTQ0 * NL], tp[(kTQ0 + 1) * NL], tp[(kTQ0 + 2) * NL], tp[kTV0 * NL],
+                         tp[(kTV0 + 1) * NL], tp[(kTV0 + 2) * NL], lqx, lqy, lqz, lvx, lvy, lvz, lmu);
         if (!real) {
             lqx = lqy = lqz = lvx = lvy = lvz = lm = lmu = 0.0;
         }

@@ -37,8 +37,8 @@ struct whg_ctx {
     long long adj_n;
     int adj_K, adj_nseg;
     bool adj_ready;
-    cudaStream_t side;        // second stream for tape recomputation (created on first use)
-    cudaEvent_t ev_tape[2], ev_back[2], ev_entry;
+    cudaStream_t side[2];     // side streams for tape recomputation (created on first use)
+    cudaEvent_t ev_tape[WHG_TAPE_BUFFERS], ev_back[WHG_TAPE_BUFFERS], ev_entry;
     // CUDA graph of graph_launches step launches of graph_chunk steps each
     cudaStream_t capture;
     cudaGraphExec_t graph;
@@ -735,7 +735,7 @@ int whg_adjoint_forward(whg_ctx* c, long long n_steps, int checkpoint_every, con
     const long long nseg = (n_steps + checkpoint_every - 1) / checkpoint_every;
     const int K = (int)(n_steps < checkpoint_every ? (n_steps > 0 ? n_steps : 1) : checkpoint_every);
     const size_t tgt = (size_t)c->S * c->Nmax * 3;
-    const size_t nd = (size_t)(nseg + 1) * 6 * NL + 2 * (size_t)K * 16 * NL + 8 * NL + tgt;
+    const size_t nd = (size_t)(nseg + 1) * 6 * NL + WHG_TAPE_BUFFERS * (size_t)K * WHG_TAPE_W * NL + 8 * NL + tgt;
     const size_t bytes = nd * sizeof(double);
     if (bytes > c->adj_bytes) {
         if (c->adj_buf) cudaFree(c->adj_buf);
@@ -751,8 +751,8 @@ int whg_adjoint_forward(whg_ctx* c, long long n_steps, int checkpoint_every, con
     a.NL = NL;
     a.ckpt = c->adj_buf;
     a.tape = a.ckpt + (size_t)(nseg + 1) * 6 * NL;
-    a.tape_len = (size_t)K * 16 * NL;
-    a.lam = a.tape + 2 * a.tape_len;
+    a.tape_len = (size_t)K * WHG_TAPE_W * NL;
+    a.lam = a.tape + WHG_TAPE_BUFFERS * a.tape_len;
     double* tcopy = a.lam + 8 * NL;
     a.target = tcopy;
     WHG_CUDA(c, cudaMemcpyAsync(tcopy, target, tgt * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
@@ -792,51 +792,58 @@ int whg_adjoint_backward(whg_ctx* c, const double* loss_weight, double* grad_pos
     const WhgLaunch l = launch_cfg(c);
     int rc = launch_check(c, whg_launch_adj_loss(c->st, c->bk, a, 1, c->opt.newton_terms, l), "adjoint start");
     if (rc) return rc;
-    if (!c->side) {
-        WHG_CUDA(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
-        for (int i = 0; i < 2; ++i) {
+    if (!c->side[0]) {
+        for (int i = 0; i < 2; ++i) WHG_CUDA(c, cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking));
+        for (int i = 0; i < WHG_TAPE_BUFFERS; ++i) {
             WHG_CUDA(c, cudaEventCreateWithFlags(&c->ev_tape[i], cudaEventDisableTiming));
             WHG_CUDA(c, cudaEventCreateWithFlags(&c->ev_back[i], cudaEventDisableTiming));
         }
         WHG_CUDA(c, cudaEventCreateWithFlags(&c->ev_entry, cudaEventDisableTiming));
     }
-    // the side stream starts after everything issued so far (checkpoints, adjoint start)
+    // the side streams start after everything issued so far (checkpoints, adjoint start)
     WHG_CUDA(c, cudaEventRecord(c->ev_entry, c->stream));
-    WHG_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_entry, 0));
-    // Segment s's products run on the context's stream while the tape of
-    // segment s-1 is recomputed on the side stream into the other buffer,
-    // once the products of segment s+1 are done with that buffer.
-    WhgLaunch side = l;
-    side.stream = c->side;
+    for (int i = 0; i < 2; ++i) WHG_CUDA(c, cudaStreamWaitEvent(c->side[i], c->ev_entry, 0));
+    // The products of segment s run on the context's stream (the critical
+    // path) while the tapes of segments s-1 and s-2 are recomputed on the two
+    // side streams, tape j into buffer j % 3 once the products of segment
+    // j + 3 are done with it.
     const int K = c->adj_K, nseg = c->adj_nseg;
     auto seg_len = [&](int seg) {
         const long long s0 = (long long)seg * K;
         return (int)(s0 + K <= c->adj_n ? K : c->adj_n - s0);
     };
+    auto tape = [&](int j, cudaStream_t stream) {
+        WhgLaunch sl = l;
+        sl.stream = stream;
+        return launch_check(c, whg_launch_adj_tape(c->st, c->bk, a, j, (long long)j * K, seg_len(j),
+                                                   j % WHG_TAPE_BUFFERS, c->opt.newton_terms, c->opt.gr_mode, sl),
+                            "adjoint tape kernel");
+    };
     if (nseg > 0) {
-        rc = launch_check(c, whg_launch_adj_tape(c->st, c->bk, a, nseg - 1, (long long)(nseg - 1) * K,
-                                                 seg_len(nseg - 1), (nseg - 1) & 1, c->opt.newton_terms,
-                                                 c->opt.gr_mode, l),
-                          "adjoint tape kernel");
+        rc = tape(nseg - 1, c->stream);
         if (rc) return rc;
     }
+    if (nseg > 1) {
+        rc = tape(nseg - 2, c->side[(nseg - 2) % 2]);
+        if (rc) return rc;
+        WHG_CUDA(c, cudaEventRecord(c->ev_tape[(nseg - 2) % WHG_TAPE_BUFFERS], c->side[(nseg - 2) % 2]));
+    }
     for (int seg = nseg - 1; seg >= 0; --seg) {
-        if (seg >= 1) {
-            const int buf = (seg - 1) & 1;
-            if (seg + 1 <= nseg - 1) WHG_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_back[buf], 0));
-            rc = launch_check(c, whg_launch_adj_tape(c->st, c->bk, a, seg - 1, (long long)(seg - 1) * K,
-                                                     seg_len(seg - 1), buf, c->opt.newton_terms,
-                                                     c->opt.gr_mode, side),
-                              "adjoint tape kernel");
+        const int j = seg - 2;
+        if (j >= 0) {
+            const int buf = j % WHG_TAPE_BUFFERS;
+            cudaStream_t side = c->side[j % 2];
+            if (j + WHG_TAPE_BUFFERS <= nseg - 1) WHG_CUDA(c, cudaStreamWaitEvent(side, c->ev_back[buf], 0));
+            rc = tape(j, side);
             if (rc) return rc;
-            WHG_CUDA(c, cudaEventRecord(c->ev_tape[buf], c->side));
+            WHG_CUDA(c, cudaEventRecord(c->ev_tape[buf], side));
         }
-        if (seg < nseg - 1) WHG_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_tape[seg & 1], 0));
-        rc = launch_check(c, whg_launch_adj_back(c->st, c->bk, a, (long long)seg * K, seg_len(seg), seg & 1,
-                                                 c->opt.newton_terms, c->opt.gr_mode, l),
+        if (seg < nseg - 1) WHG_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_tape[seg % WHG_TAPE_BUFFERS], 0));
+        rc = launch_check(c, whg_launch_adj_back(c->st, c->bk, a, (long long)seg * K, seg_len(seg),
+                                                 seg % WHG_TAPE_BUFFERS, c->opt.newton_terms, c->opt.gr_mode, l),
                           "adjoint back kernel");
         if (rc) return rc;
-        WHG_CUDA(c, cudaEventRecord(c->ev_back[seg & 1], c->stream));
+        WHG_CUDA(c, cudaEventRecord(c->ev_back[seg % WHG_TAPE_BUFFERS], c->stream));
     }
     return launch_check(c, whg_launch_adj_finish(c->st, c->bk, a, l), "adjoint finish kernel");
 }
@@ -851,14 +858,14 @@ void whg_destroy(whg_ctx* c)
     if (c->q_next) cudaFree(c->q_next);
     if (c->st.dbg) cudaFree(c->st.dbg);
     if (c->adj_buf) cudaFree(c->adj_buf);
-    if (c->side) {
-        cudaStreamSynchronize(c->side);
-        for (int i = 0; i < 2; ++i) {
+    if (c->side[0]) {
+        for (int i = 0; i < 2; ++i) cudaStreamSynchronize(c->side[i]);
+        for (int i = 0; i < WHG_TAPE_BUFFERS; ++i) {
             cudaEventDestroy(c->ev_tape[i]);
             cudaEventDestroy(c->ev_back[i]);
         }
         cudaEventDestroy(c->ev_entry);
-        cudaStreamDestroy(c->side);
+        for (int i = 0; i < 2; ++i) cudaStreamDestroy(c->side[i]);
     }
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->capture) cudaStreamDestroy(c->capture);

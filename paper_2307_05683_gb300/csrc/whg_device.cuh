@@ -331,11 +331,19 @@ __device__ __forceinline__ void stumpff_c2c3_f32(float z, float& c2, float& c3)
 // (quadratic convergence: 1e-7 -> 1e-14 -> rounding), so the result keeps
 // FP64 accuracy wherever the FP64 Halley phase converges, while ~60 FP64
 // operations per drift move to the FP32 pipe.  No other branches.
-// Returns beta > 0; Xout receives the final universal variable.
-template <int NT>
+// Returns beta > 0; Xout receives the final universal variable.  With
+// VALS, *dv also receives the drift's intermediate values (for the adjoint's
+// tape); the arithmetic is the same either way.
+struct DriftVals {
+    double r0i, r0, eta0, beta;          // of the initial state
+    double G1, G2, G3;                   // Stiefel functions at the final X
+    double ri, A, fm1, g, fd, gdm1;      // 1/r, mu/r0, Lagrange coefficients
+};
+
+template <int NT, bool VALS = false>
 __device__ __forceinline__ bool kepler_drift(double mu, double h, double& qx, double& qy,
                                              double& qz, double& vx, double& vy, double& vz,
-                                             double& Xout, bool h32 = false)
+                                             double& Xout, bool h32 = false, DriftVals* dv = nullptr)
 {
     const double r0sq = fma(qx, qx, fma(qy, qy, qz * qz));
     const double r0i = rsqrt(r0sq);
@@ -414,6 +422,11 @@ __device__ __forceinline__ bool kepler_drift(double mu, double h, double& qx, do
     vz = fma(fd, qz, fma(gdm1, vz, vz));
     qx = nqx; qy = nqy; qz = nqz;
     Xout = Xf;
+    if constexpr (VALS) {
+        dv->r0i = r0i; dv->r0 = r0; dv->eta0 = eta0; dv->beta = beta;
+        dv->G1 = G1f; dv->G2 = G2f; dv->G3 = G3f;
+        dv->ri = ri; dv->A = mr0; dv->fm1 = fm1; dv->g = g; dv->fd = fd; dv->gdm1 = gdm1;
+    }
     return beta > 0.0;
 }
 
@@ -569,10 +582,41 @@ __device__ __forceinline__ void jump(const Group<L>& g, double m, double jc, dou
 // evaluated by both of its lanes: 7 reciprocal square roots per lane for
 // L = 8); the close-encounter test then uses the distances k <= L/2, which
 // cover every pair from one side.
-template <int L, int GRM>
+// With GEOM (the adjoint's tape kernel), the factors of the kick's
+// vector-Jacobian product that do not depend on the adjoints are written to
+// kt: pair round r (partner j at distance k = r + 1 <= L/2, this lane i) at
+// kt.p[(8r + n) kt.NL], n = 0..7: Q_j - Q_i (3), hm_j r^-3, hm_i r^-3,
+// 3 hm_j r^-5, 3 hm_i r^-5, dt r^-3; the GR factors at kt.p[(32 + n) kt.NL]:
+// c = kgr/|Q|^4, 4 c/|Q|^2, 2 c/m0.  The velocities come out the same.
+struct KickTape {
+    double* p;
+    size_t NL;
+    double dt, two_muinv;
+};
+constexpr int kKickTapeRound = 8;
+
+template <bool GEOM>
+__device__ __forceinline__ void kick_geom(const KickTape* kt, int round, double dx, double dy, double dz,
+                                          double r2, double r3, double hmj, double hmi)
+{
+    if constexpr (GEOM) {
+        double* t = kt->p + (size_t)(kKickTapeRound * round) * kt->NL;
+        const double r5x3 = 3.0 * (r3 * rcp(r2));
+        t[0] = dx;
+        t[kt->NL] = dy;
+        t[2 * kt->NL] = dz;
+        t[3 * kt->NL] = hmj * r3;
+        t[4 * kt->NL] = hmi * r3;
+        t[5 * kt->NL] = hmj * r5x3;
+        t[6 * kt->NL] = hmi * r5x3;
+        t[7 * kt->NL] = kt->dt * r3;
+    }
+}
+
+template <int L, int GRM, bool GEOM = false>
 __device__ __forceinline__ bool kick(const Group<L>& g, double qx, double qy, double qz, double hm,
                                      double mrat, double kgr, const double* thr2, double& vx,
-                                     double& vy, double& vz, bool full = false)
+                                     double& vy, double& vz, bool full = false, const KickTape* kt = nullptr)
 {
     bool close = false;
     if (full) {
@@ -585,7 +629,9 @@ __device__ __forceinline__ bool kick(const Group<L>& g, double qx, double qy, do
             const double hmj = __shfl_sync(WHG_FULL_MASK, hm, to);
             const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
             if (2 * k <= L) close |= __double_as_longlong(r2) < __double_as_longlong(thr2[k - 1]);
-            const double sj = hmj * rsqrt_cubed(r2);
+            const double r3 = rsqrt_cubed(r2);
+            if (2 * k <= L) kick_geom<GEOM>(kt, k - 1, dx, dy, dz, r2, r3, hmj, hm);
+            const double sj = hmj * r3;
             vx = fma(sj, dx, vx);
             vy = fma(sj, dy, vy);
             vz = fma(sj, dz, vz);
@@ -601,6 +647,7 @@ __device__ __forceinline__ bool kick(const Group<L>& g, double qx, double qy, do
             const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
             close |= __double_as_longlong(r2) < __double_as_longlong(thr2[k - 1]);
             const double r3 = rsqrt_cubed(r2);
+            kick_geom<GEOM>(kt, k - 1, dx, dy, dz, r2, r3, hmj, hm);
             const double sj = hmj * r3;
             vx = fma(sj, dx, vx);
             vy = fma(sj, dy, vy);
@@ -622,7 +669,9 @@ __device__ __forceinline__ bool kick(const Group<L>& g, double qx, double qy, do
             const double hmj = __shfl_sync(WHG_FULL_MASK, hm, to);
             const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
             close |= __double_as_longlong(r2) < __double_as_longlong(thr2[L / 2 - 1]);
-            const double sj = hmj * rsqrt_cubed(r2);
+            const double r3 = rsqrt_cubed(r2);
+            kick_geom<GEOM>(kt, L / 2 - 1, dx, dy, dz, r2, r3, hmj, hm);
+            const double sj = hmj * r3;
             vx = fma(sj, dx, vx);
             vy = fma(sj, dy, vy);
             vz = fma(sj, dz, vz);
@@ -632,6 +681,12 @@ __device__ __forceinline__ bool kick(const Group<L>& g, double qx, double qy, do
         // a_GR(Q) = -6 (G m0)^2 Q / (c^2 |Q|^4); kgr = -6 m0^2 dt / c^2.
         const double ri2 = rcp(fma(qx, qx, fma(qy, qy, qz * qz)));
         const double c = kgr * (ri2 * ri2);
+        if constexpr (GEOM) {
+            double* t = kt->p + (size_t)(4 * kKickTapeRound) * kt->NL;
+            t[0] = c;
+            t[kt->NL] = 4.0 * c * ri2;
+            t[2 * kt->NL] = c * kt->two_muinv;
+        }
         if (GRM == 1) {
             vx = fma(c, qx, vx);
             vy = fma(c, qy, vy);
