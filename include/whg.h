@@ -216,20 +216,23 @@ int whg_set_raw(whg_ctx* ctx, const double* Q, const double* v, const long long*
  * with Q_i(T) the heliocentric positions of the synchronized state after
  * n_steps Wisdom-Holman steps (Eq. 2).  Needs a context initialised with
  * whg_init / whg_init_device and not stepped since.  Advances the state by
- * n_steps exactly as whg_step does, keeping the state every checkpoint_every
- * steps in device memory owned by ctx (about (n/K + 1) * 48 B + K * 128 B per
- * planet lane).  target [S][N][3] and loss [S] are DEVICE pointers; target is
- * copied.  Async. */
+ * n_steps exactly as whg_step does (without repacking stopped systems, so
+ * that every checkpoint has the same layout), keeping the state every
+ * checkpoint_every steps in device memory owned by ctx: about
+ * (n/K + 1) * 48 B + 3 * K * 592 B per planet lane (checkpoints and three
+ * tape buffers).  target [S][N][3] and loss [S] are DEVICE pointers; target
+ * is copied.  Async. */
 int whg_adjoint_forward(whg_ctx* ctx, long long n_steps, int checkpoint_every, const double* target,
                         double* loss);
 
 /* Backward half: gradients of sum_s w_s L_s with respect to the inputs of the
  * last init (inertial positions and velocities [S][1+N][3], masses [S][1+N],
  * star included), w_s = loss_weight[s] (DEVICE [S], NULL = all 1).  Each K-step
- * segment is recomputed from its checkpoint while a per-step tape is kept, and
- * the vector-Jacobian products of J, I (+GR), J and K (the Kepler flow through
- * the implicit function theorem at the converged universal variable) are
- * applied in reverse.  Output pointers are DEVICE pointers (any may be NULL);
+ * segment is recomputed from its checkpoint while a per-step tape is kept,
+ * and the vector-Jacobian products of J, I (+GR), J and K (the Kepler flow
+ * through the implicit function theorem at the converged universal variable)
+ * are applied in reverse.  Output pointers are DEVICE pointers (any may be
+ * NULL);
  * systems that froze during the forward half get NaN.  May be called again
  * with other weights.  Async. */
 int whg_adjoint_backward(whg_ctx* ctx, const double* loss_weight, double* grad_pos, double* grad_vel,

@@ -240,6 +240,13 @@ __device__ __forceinline__ void jump_vjp(const Group<L>& g, double m, double c, 
     lmu = fma(-cmu * m, vd, lmu);
 }
 
+// Hint that the line holding *p will be read soon: fetched into L2, no
+// register written and no fault on any address.
+__device__ __forceinline__ void prefetch_l2(const double* p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Tape layout: per lane and step, WHG_TAPE_W doubles at stride NL.  Besides
 // the state the back kernel needs (velocities for the jumps, positions for
 // the GR term, the drift input), the tape holds everything of the kick and
@@ -482,6 +489,11 @@ __device__ __forceinline__ void back_body(const WhgState& st, const WhgBuckets& 
     double lm = lam[6 * NL + lane], lmu = lam[7 * NL + lane];
     for (int k = nk - 1; k >= 0; --k) {
         const double* tp = tape + (size_t)k * WHG_TAPE_W * NL + lane;
+        if (k >= 2) {                                 // this step's fields two steps ahead, into L2
+            const double* pf = tp - (size_t)2 * WHG_TAPE_W * NL;
+#pragma unroll
+            for (int f = 0; f < WHG_TAPE_W; ++f) prefetch_l2(pf + (size_t)f * NL);
+        }
         const bool merged = GRM == 0 && st.merge;
         if (!merged)
             jump_vjp<L>(g, m, c, cmu, tp[kTV3 * NL], tp[(kTV3 + 1) * NL], tp[(kTV3 + 2) * NL], lqx, lqy, lqz,

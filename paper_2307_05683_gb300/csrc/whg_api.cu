@@ -510,11 +510,10 @@ int whg_init_device(whg_ctx* c, const double* masses, const double* pos, const d
     return init_common(c, in, nullptr);
 }
 
-int whg_step(whg_ctx* c, long long n)
+// n steps; repack = false (the adjoint's forward half) keeps every system on
+// its lanes: no repack, and no replay of a captured graph that holds one.
+static int step_impl(whg_ctx* c, long long n, bool repack)
 {
-    if (!c) return WHG_EINVAL;
-    if (!c->initialized) return fail(c, WHG_ESTATE, "whg_step before whg_init");
-    if (n < 0) return fail(c, WHG_EINVAL, "n_steps=%lld must be >= 0", n);
     long long chunk = c->opt.steps_per_launch;
     if (chunk <= 0) {
         // about 5e7 system-steps per launch (a few tenths of a second)
@@ -525,7 +524,7 @@ int whg_step(whg_ctx* c, long long n)
     if (c->host_nstep >= 0) c->host_nstep += n;
     c->adj_ready = false;
     const long long G = c->opt.graph_launches;
-    if (G > 0 && n >= G * chunk) {
+    if (G > 0 && n >= G * chunk && (repack || !c->repack_buf)) {
         if (!c->graph || c->graph_chunk != chunk) {      // capture G launches once
             if (c->graph) {
                 cudaGraphExecDestroy(c->graph);
@@ -563,13 +562,21 @@ int whg_step(whg_ctx* c, long long n)
         int rc = launch_check(c, launch_steps(c, k, l), "step kernel");
         if (rc) return rc;
         n -= k;
-        if (c->repack_buf && ++c->since_repack >= every) {
+        if (repack && c->repack_buf && ++c->since_repack >= every) {
             WHG_CUDA(c, enqueue_repack(c, c->stream));
             c->launches += 2;
             c->since_repack = 0;
         }
     }
     return WHG_OK;
+}
+
+int whg_step(whg_ctx* c, long long n)
+{
+    if (!c) return WHG_EINVAL;
+    if (!c->initialized) return fail(c, WHG_ESTATE, "whg_step before whg_init");
+    if (n < 0) return fail(c, WHG_EINVAL, "n_steps=%lld must be >= 0", n);
+    return step_impl(c, n, true);
 }
 
 int whg_read_state_device(whg_ctx* c, double* pos, double* vel, int* status, double* t)
@@ -722,6 +729,37 @@ int whg_test_queue_timeout(whg_ctx* c, long long spin_limit, int* flag)
 
 const char* whg_last_error(const whg_ctx* c) { return c ? c->err : g_create_err; }
 
+// Side streams and events of the adjoint (created on first use).
+static int adjoint_streams(whg_ctx* c)
+{
+    if (c->side[0]) return WHG_OK;
+    for (int i = 0; i < 2; ++i) WHG_CUDA(c, cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking));
+    for (int i = 0; i < WHG_TAPE_BUFFERS; ++i) {
+        WHG_CUDA(c, cudaEventCreateWithFlags(&c->ev_tape[i], cudaEventDisableTiming));
+        WHG_CUDA(c, cudaEventCreateWithFlags(&c->ev_back[i], cudaEventDisableTiming));
+    }
+    WHG_CUDA(c, cudaEventCreateWithFlags(&c->ev_entry, cudaEventDisableTiming));
+    return WHG_OK;
+}
+
+// Tape buffer of segment j (WHG_TAPE_BUFFERS rotating buffers).
+static int tape_buffer(int j) { return j % WHG_TAPE_BUFFERS; }
+
+static int segment_length(const whg_ctx* c, int seg)
+{
+    const long long s0 = (long long)seg * c->adj_K;
+    return (int)(s0 + c->adj_K <= c->adj_n ? c->adj_K : c->adj_n - s0);
+}
+
+static int launch_tape(whg_ctx* c, const WhgAdj& a, int j, cudaStream_t stream)
+{
+    WhgLaunch l = launch_cfg(c);
+    l.stream = stream;
+    return launch_check(c, whg_launch_adj_tape(c->st, c->bk, a, j, (long long)j * c->adj_K, segment_length(c, j),
+                                               tape_buffer(j), c->opt.newton_terms, c->opt.gr_mode, l),
+                        "adjoint tape kernel");
+}
+
 int whg_adjoint_forward(whg_ctx* c, long long n_steps, int checkpoint_every, const double* target,
                         double* loss)
 {
@@ -735,7 +773,8 @@ int whg_adjoint_forward(whg_ctx* c, long long n_steps, int checkpoint_every, con
     const long long nseg = (n_steps + checkpoint_every - 1) / checkpoint_every;
     const int K = (int)(n_steps < checkpoint_every ? (n_steps > 0 ? n_steps : 1) : checkpoint_every);
     const size_t tgt = (size_t)c->S * c->Nmax * 3;
-    const size_t nd = (size_t)(nseg + 1) * 6 * NL + WHG_TAPE_BUFFERS * (size_t)K * WHG_TAPE_W * NL + 8 * NL + tgt;
+    const size_t tape_len = (size_t)K * WHG_TAPE_W * NL;
+    const size_t nd = (size_t)(nseg + 1) * 6 * NL + WHG_TAPE_BUFFERS * tape_len + 8 * NL + tgt;
     const size_t bytes = nd * sizeof(double);
     if (bytes > c->adj_bytes) {
         if (c->adj_buf) cudaFree(c->adj_buf);
@@ -751,28 +790,31 @@ int whg_adjoint_forward(whg_ctx* c, long long n_steps, int checkpoint_every, con
     a.NL = NL;
     a.ckpt = c->adj_buf;
     a.tape = a.ckpt + (size_t)(nseg + 1) * 6 * NL;
-    a.tape_len = (size_t)K * WHG_TAPE_W * NL;
-    a.lam = a.tape + WHG_TAPE_BUFFERS * a.tape_len;
+    a.tape_len = tape_len;
+    a.lam = a.tape + WHG_TAPE_BUFFERS * tape_len;
     double* tcopy = a.lam + 8 * NL;
     a.target = tcopy;
+    c->adj_n = n_steps;
+    c->adj_K = K;
+    c->adj_nseg = (int)nseg;
+    c->adj_ready = false;
     WHG_CUDA(c, cudaMemcpyAsync(tcopy, target, tgt * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    int rc = adjoint_streams(c);
+    if (rc) return rc;
     const WhgLaunch l = launch_cfg(c);
     for (long long seg = 0; seg < nseg; ++seg) {
-        int rc = launch_check(c, whg_launch_adj_save(c->st, c->bk, a, (int)seg, l), "checkpoint kernel");
+        rc = launch_check(c, whg_launch_adj_save(c->st, c->bk, a, (int)seg, l), "checkpoint kernel");
         if (rc) return rc;
         const long long k = (seg + 1) * checkpoint_every <= n_steps ? checkpoint_every
                                                                      : n_steps - seg * checkpoint_every;
-        rc = whg_step(c, k);
+        rc = step_impl(c, k, false);
         if (rc) return rc;
     }
-    int rc = launch_check(c, whg_launch_adj_save(c->st, c->bk, a, (int)nseg, l), "checkpoint kernel");
+    rc = launch_check(c, whg_launch_adj_save(c->st, c->bk, a, (int)nseg, l), "checkpoint kernel");
     if (rc) return rc;
     a.loss = loss;
     rc = launch_check(c, whg_launch_adj_loss(c->st, c->bk, a, 0, c->opt.newton_terms, l), "loss kernel");
     if (rc) return rc;
-    c->adj_n = n_steps;
-    c->adj_K = checkpoint_every;
-    c->adj_nseg = (int)nseg;
     c->adj_ready = true;
     return WHG_OK;
 }
@@ -792,58 +834,43 @@ int whg_adjoint_backward(whg_ctx* c, const double* loss_weight, double* grad_pos
     const WhgLaunch l = launch_cfg(c);
     int rc = launch_check(c, whg_launch_adj_loss(c->st, c->bk, a, 1, c->opt.newton_terms, l), "adjoint start");
     if (rc) return rc;
-    if (!c->side[0]) {
-        for (int i = 0; i < 2; ++i) WHG_CUDA(c, cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking));
-        for (int i = 0; i < WHG_TAPE_BUFFERS; ++i) {
-            WHG_CUDA(c, cudaEventCreateWithFlags(&c->ev_tape[i], cudaEventDisableTiming));
-            WHG_CUDA(c, cudaEventCreateWithFlags(&c->ev_back[i], cudaEventDisableTiming));
-        }
-        WHG_CUDA(c, cudaEventCreateWithFlags(&c->ev_entry, cudaEventDisableTiming));
-    }
-    // the side streams start after everything issued so far (checkpoints, adjoint start)
+    rc = adjoint_streams(c);
+    if (rc) return rc;
+    // the side streams start after everything issued so far (checkpoints,
+    // adjoint start)
     WHG_CUDA(c, cudaEventRecord(c->ev_entry, c->stream));
     for (int i = 0; i < 2; ++i) WHG_CUDA(c, cudaStreamWaitEvent(c->side[i], c->ev_entry, 0));
     // The products of segment s run on the context's stream (the critical
     // path) while the tapes of segments s-1 and s-2 are recomputed on the two
-    // side streams, tape j into buffer j % 3 once the products of segment
+    // side streams: tape j into buffer j % 3 once the products of segment
     // j + 3 are done with it.
-    const int K = c->adj_K, nseg = c->adj_nseg;
-    auto seg_len = [&](int seg) {
-        const long long s0 = (long long)seg * K;
-        return (int)(s0 + K <= c->adj_n ? K : c->adj_n - s0);
-    };
-    auto tape = [&](int j, cudaStream_t stream) {
-        WhgLaunch sl = l;
-        sl.stream = stream;
-        return launch_check(c, whg_launch_adj_tape(c->st, c->bk, a, j, (long long)j * K, seg_len(j),
-                                                   j % WHG_TAPE_BUFFERS, c->opt.newton_terms, c->opt.gr_mode, sl),
-                            "adjoint tape kernel");
-    };
+    const int nseg = c->adj_nseg;
     if (nseg > 0) {
-        rc = tape(nseg - 1, c->stream);
+        rc = launch_tape(c, a, nseg - 1, c->stream);
         if (rc) return rc;
     }
     if (nseg > 1) {
-        rc = tape(nseg - 2, c->side[(nseg - 2) % 2]);
+        rc = launch_tape(c, a, nseg - 2, c->side[(nseg - 2) % 2]);
         if (rc) return rc;
-        WHG_CUDA(c, cudaEventRecord(c->ev_tape[(nseg - 2) % WHG_TAPE_BUFFERS], c->side[(nseg - 2) % 2]));
+        WHG_CUDA(c, cudaEventRecord(c->ev_tape[tape_buffer(nseg - 2)], c->side[(nseg - 2) % 2]));
     }
     for (int seg = nseg - 1; seg >= 0; --seg) {
         const int j = seg - 2;
         if (j >= 0) {
-            const int buf = j % WHG_TAPE_BUFFERS;
             cudaStream_t side = c->side[j % 2];
-            if (j + WHG_TAPE_BUFFERS <= nseg - 1) WHG_CUDA(c, cudaStreamWaitEvent(side, c->ev_back[buf], 0));
-            rc = tape(j, side);
+            if (j + WHG_TAPE_BUFFERS <= nseg - 1)
+                WHG_CUDA(c, cudaStreamWaitEvent(side, c->ev_back[tape_buffer(j)], 0));
+            rc = launch_tape(c, a, j, side);
             if (rc) return rc;
-            WHG_CUDA(c, cudaEventRecord(c->ev_tape[buf], side));
+            WHG_CUDA(c, cudaEventRecord(c->ev_tape[tape_buffer(j)], side));
         }
-        if (seg < nseg - 1) WHG_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_tape[seg % WHG_TAPE_BUFFERS], 0));
-        rc = launch_check(c, whg_launch_adj_back(c->st, c->bk, a, (long long)seg * K, seg_len(seg),
-                                                 seg % WHG_TAPE_BUFFERS, c->opt.newton_terms, c->opt.gr_mode, l),
+        if (seg < nseg - 1) WHG_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_tape[tape_buffer(seg)], 0));
+        rc = launch_check(c, whg_launch_adj_back(c->st, c->bk, a, (long long)seg * c->adj_K,
+                                                 segment_length(c, seg), tape_buffer(seg),
+                                                 c->opt.newton_terms, c->opt.gr_mode, l),
                           "adjoint back kernel");
         if (rc) return rc;
-        WHG_CUDA(c, cudaEventRecord(c->ev_back[seg % WHG_TAPE_BUFFERS], c->stream));
+        WHG_CUDA(c, cudaEventRecord(c->ev_back[tape_buffer(seg)], c->stream));
     }
     return launch_check(c, whg_launch_adj_finish(c->st, c->bk, a, l), "adjoint finish kernel");
 }

@@ -193,6 +193,23 @@ def test_adjoint_entries_match_two_point_central_differences(whg):
           f"system's largest within {rel[big].max():.1e} relative; all within {floor:.1e} of the largest")
 
 
+def test_adjoint_forward_keeps_systems_on_their_lanes(whg):
+    """With a stop rule on, whg_step regroups stopped systems (repacking) by
+    default; the adjoint's forward half must not, since every checkpoint
+    and tape refers to the lanes of the initial layout.  Gradients of the
+    systems still running equal those with repacking off, bit for bit."""
+    ens = inputs.compact_ensemble(37, 700)
+    T = _targets(ens, 7)
+    kw = dict(close_encounter_hill=8.0, eject_factor=3.0, steps_per_launch=25)
+    auto = gpu_grad(whg, ens, T, 1500, 25, **kw)
+    off = gpu_grad(whg, ens, T, 1500, 25, repack_frozen=False, **kw)
+    stopped = np.isnan(auto[3]).any(axis=1)
+    assert 50 < stopped.sum() < 650                  # systems stop during the forward half
+    assert np.array_equal(np.isnan(off[3]).any(axis=1), stopped)
+    for x, y in zip(auto, off):
+        assert np.array_equal(x, y, equal_nan=True)
+
+
 def test_autograd_function_matches_c_abi(whg):
     import torch
     from paper_2307_05683_gb300.autograd import final_position_loss
