@@ -10,9 +10,10 @@
 // spends integer and FP32 work freely to save FP64 instructions:
 //   * reciprocals and reciprocal square roots start from the FP32 hardware
 //     approximation of a mantissa built with integer operations and take one
-//     third-order FP64 refinement whose exact pieces (1 - x y, y^2, y^3) are
-//     formed on the integer pipe (1/x: 2, x^(-1/2) and x^(-3/2): 4 FP64
-//     instructions), and the solver's factors -1/2 are exponent decrements;
+//     third-order refinement whose correction (from the exact 1 - x y or
+//     1 - x y^2) is formed in fixed point on the integer pipe, leaving one
+//     FP64 FMA per call, and the solver's factors -1/2 are exponent
+//     decrements;
 //   * the all-pairs interaction uses Newton's third law (Sec. 3.3), with
 //     partner schedules that suit warp shuffles rather than AVX512 lanes;
 //   * cross-lane sums of 3-vectors are reduce-scatters by xor partners when L
@@ -43,9 +44,11 @@ namespace whg {
 // integer arithmetic so that every normal double works.  With e = 1 - x y0
 // (resp. e = 1 - x y0^2) the third-order steps are
 //     1/x       = y0 (1 + e + e^2 + ...)          ->  y0 + y0 (e + e^2)
-//     1/sqrt(x) = y0 (1 + e/2 + 3e^2/8 + ...)     ->  y0 + y0 e (1/2 + 3e/8)
-// whose truncation error (~e^3 < 2^-63) is far below double rounding; results
-// are within about one ulp of the exact value.
+//     1/sqrt(x) = y0 (1 + e/2 + 3e^2/8 + ...)     ->  y0 + y0 (e/2 + 3e^2/8)
+// whose truncation error (~e^3 < 2^-61) is far below double rounding; results
+// are within about one ulp of the exact value.  e is exact in integer
+// arithmetic (the seed has 24 significant bits), and so is the correction to
+// the precision it needs, so only the final y0 + y0 t is an FP64 operation.
 
 __device__ __forceinline__ float approx_rcp_f32(float x)
 {
@@ -64,9 +67,9 @@ __device__ __forceinline__ float approx_rsqrt_f32(float x)
 // ------------------------------------------------------------------------
 // Integer-pipe pieces of the reciprocal and reciprocal square root.  On this
 // GPU an FP64 warp instruction holds the FP64 pipe for 64 cycles and an
-// integer one its pipe for about 1, so exact integer forms replace FP64
-// operations wherever the operands are short: the seeds y below carry 24
-// significant bits (an FP32 approximation widened to FP64).
+// integer one its pipe for about 1, so integer forms replace FP64 operations
+// wherever the operands are short: the seeds y below carry 24 significant
+// bits (an FP32 approximation widened to FP64).
 
 // D 2^-s rounded to the nearest double (ties to even); D a signed 64-bit
 // integer, the result a normal double or zero.
@@ -122,9 +125,12 @@ __device__ __forceinline__ unsigned long long significand(unsigned hi, unsigned 
 // 1/x for finite x with 2^-1022 <= |x| < 2^1021 (either sign; 1/x normal):
 // FP32 seed y (24 bits), then
 // y (1 + e + e^2) with e = 1 - x y.  The seed is within ~2^-22 of 1/x, so
-// x y = 2^s - D with |D| < 2^55 and s = 202 - (y's FP32 exponent) >= 64:
-// D = -(Mx My mod 2^64) in wrap-around integer arithmetic, and e = D 2^-s
-// rounded once, the value fma(-x, y, 1) gives.  2 FP64 operations.
+// x y = 2^s - D with |D| < 2^55 and s = 202 - (y's FP32 exponent) in 75..76:
+// D = -(Mx My mod 2^64) in wrap-around integer arithmetic, so e = D 2^-s
+// exactly.  The correction t = e + e^2 is formed in the same fixed point (e^2
+// from the top 31 bits of D: relative error 2^-30 of a term below 2^-43) and
+// rounded once to a double; 1/x = fma(y, t, y), within one ulp (the neglected
+// e^3 is below 2^-65).  1 FP64 operation.
 __device__ __forceinline__ double rcp(double x)
 {
     const unsigned hi = (unsigned)__double2hiint(x);
@@ -138,41 +144,50 @@ __device__ __forceinline__ double rcp(double x)
     const double y = __hiloint2double((int)yhi, (int)(rb << 29));
     const unsigned long long My = (rb & 0x007fffffu) | 0x00800000u;
     const long long D = (long long)(0ULL - significand(hi, lo) * My);
-    double e = scaled_int_to_double(D, 202 - erb);
+    const int sc = 202 - erb;                                           // 75..76
+    const long long Dh = D >> 24;                                       // |Dh| < 2^31
+    const long long T = D + ((Dh * Dh) >> ((sc - 48) & 63));            // (e + e^2) 2^sc
+    double t = scaled_int_to_double(T, sc);
     // outside the domain keep the IEEE outcome of the FP64 form: zero and
     // subnormal x give an infinite result, inf and NaN a NaN
-    e = ex == 0 ? __longlong_as_double(0x7ff0000000000000LL) : e;
-    e = ex == 0x7ff ? __longlong_as_double(0x7ff8000000000000LL) : e;
-    return fma(y, fma(e, e, e), y);
+    t = ex == 0 ? __longlong_as_double(0x7ff0000000000000LL) : t;
+    t = ex == 0x7ff ? __longlong_as_double(0x7ff8000000000000LL) : t;
+    return fma(y, t, y);
 }
 
-// Seed of x^(-1/2) for finite normal 0 < x < 2^1022: y (24-bit significand
-// My, biased exponent dex), y^2 exactly (48 bits) and y^3 rounded to nearest,
-// all on the integer pipe.
-struct RsqrtSeed {
-    double y, y2, y3;
-};
-
+// x^(-1/2) and x^(-3/2) for finite normal x > 0 (x^(-3/2) normal for
+// 2^-681 < x < 2^682: the 1/r^3 of a pair from r^2), from the seed y of
+// rsqrt.approx on an FP32 copy of the mantissa (24-bit significand My, the
+// exponent handled with integers), with the whole correction on the integer
+// pipe and a single FP64 operation:
+//     x^(-1/2) = y   (1 - e)^(-1/2) = y   (1 + e/2  + 3e^2/8  + ...),
+//     x^(-3/2) = y^3 (1 - e)^(-3/2) = y^3 (1 + 3e/2 + 15e^2/8 + ...),
+// e = 1 - x y^2.  y^3 is rounded to nearest from the exact My^3 (72 bits).
+// x = Mx 2^(ex-52) (53-bit significand Mx) and y^2 = S 2^(2 dex - 2092)
+// (S = My^2, 48 bits) give x y^2 = P 2^-s with P = Mx S (101 bits, two
+// 64-bit products) and s = 2144 - ex - 2 dex (98..101), so e = (2^s - P) 2^-s
+// exactly, |e| < 2^-21 (the FP32 seed's error).  E = e 2^83 fits an int64; the
+// correction u = a e + b e^2 is formed from E in fixed point (e^2 from the
+// top 32 bits of E: relative error 2^-30 of a term below 2^-42) and rounded
+// once to a double, and the result is fma(w, u, w) with w = y or y^3: within
+// about one ulp, the neglected terms (~e^3) being below 2^-61.  Zero and
+// subnormal x give +inf, inf and NaN give NaN.
 template <bool CUBE>
-__device__ __forceinline__ RsqrtSeed rsqrt_seed(double x)
+__device__ __forceinline__ double rsqrt_pow(double x)
 {
     const unsigned hi = (unsigned)__double2hiint(x);
     const unsigned lo = (unsigned)__double2loint(x);
-    const int ex = (int)((hi >> 20) & 0x7ffu) - 1023;                  // unbiased exponent
+    const unsigned ef = (hi >> 20) & 0x7ffu;
+    const int ex = (int)ef - 1023;                                     // unbiased exponent
     const int odd = ex & 1;
     const int half = (ex - odd) / 2;                                   // x = 4^half * mant
     const float mant = __uint_as_float(((unsigned)(127 + odd) << 23) | ((hi & 0x000fffffu) << 3) |
                                        (lo >> 29));                    // in [1, 4)
     const unsigned rb = __float_as_uint(approx_rsqrt_f32(mant));       // in (0.5, 1]
-    const int dex = (int)((rb >> 23) & 0xffu) - 127 - half + 1023;
-    RsqrtSeed r;
-    r.y = __hiloint2double((int)(((unsigned)dex << 20) | ((rb >> 3) & 0x000fffffu)), (int)(rb << 29));
+    const int dex = (int)((rb >> 23) & 0xffu) - 127 - half + 1023;     // biased exponent of y
     const unsigned long long My = (rb & 0x007fffffu) | 0x00800000u;
     const unsigned long long S = My * My;                              // [2^46, 2^48), exact
-    const unsigned long long top = S >> 47;
-    const unsigned long long f2 = (S << (6 - top)) & 0x000fffffffffffffULL;
-    r.y2 = exp_bits_to_double(2 * dex - 1023 + (long long)top, f2);
-    r.y3 = 0.0;
+    double w;
     if (CUBE) {                                                        // My^3 in [2^69, 2^72)
         const unsigned long long clo = S * My, chi = __umul64hi(S, My);
         const int p = 127 - __clzll((long long)chi);                   // leading-one position
@@ -182,32 +197,29 @@ __device__ __forceinline__ RsqrtSeed rsqrt_seed(double x)
         m += (rem > hb || (rem == hb && (m & 1ULL))) ? 1ULL : 0ULL;
         const unsigned long long carry = m >> 53;
         m >>= carry;
-        const long long E = p + 3 * dex - 2115 + (long long)carry;
-        r.y3 = exp_bits_to_double(E, m & 0x000fffffffffffffULL);
+        const long long E3 = p + 3 * dex - 2115 + (long long)carry;
+        w = exp_bits_to_double(E3, m & 0x000fffffffffffffULL);
+    } else {
+        w = __hiloint2double((int)(((unsigned)dex << 20) | ((rb >> 3) & 0x000fffffu)), (int)(rb << 29));
     }
+    const unsigned long long Mx = significand(hi, lo);
+    const unsigned long long plo = Mx * S, phi = __umul64hi(Mx, S);
+    const int s = 2144 - ex - 2 * dex;                                 // 98..101 for normal x
+    const unsigned long long dlo = 0ULL - plo;
+    const unsigned long long dhi = (1ULL << ((s - 64) & 63)) - phi - (plo != 0ULL ? 1ULL : 0ULL);
+    const int sr = (s - 83) & 63;                                      // 15..18
+    const long long E = (long long)((dlo >> sr) | (dhi << ((64 - sr) & 63)));   // e 2^83
+    const long long Eh = E >> 32;                                      // e 2^51
+    const long long E2 = (Eh * Eh) >> 22;                              // e^2 2^80
+    const long long U = CUBE ? E + (E >> 1) + 15 * E2 : (E >> 1) + 3 * E2;   // u 2^83
+    double r = fma(w, scaled_int_to_double(U, 83), w);
+    r = ef == 0u ? __longlong_as_double(0x7ff0000000000000LL) : r;
+    r = ef == 0x7ffu ? __longlong_as_double(0x7ff8000000000000LL) : r;
     return r;
 }
 
-// 1/sqrt(x) for finite normal 0 < x < 2^1022: y (1 + e/2 + 3e^2/8),
-// e = 1 - x y^2.  4 FP64 operations.
-__device__ __forceinline__ double rsqrt(double x)
-{
-    const RsqrtSeed r = rsqrt_seed<false>(x);
-    const double e = fma(-x, r.y2, 1.0);
-    return fma(r.y * e, fma(0.375, e, 0.5), r.y);
-}
-
-// x^(-3/2) for 2^-681 < x < 2^682 (the result a normal double; the 1/r^3
-// of a pair from r^2),
-// straight from the rsqrt seed: x^(-3/2) = y^3 (1 - e)^(-3/2) = y^3 (1 +
-// 3e/2 + 15e^2/8 + ...) with e = 1 - x y^2; truncation ~ (35/16) e^3 < 2^-61.
-// 4 FP64 operations.
-__device__ __forceinline__ double rsqrt_cubed(double x)
-{
-    const RsqrtSeed r = rsqrt_seed<true>(x);
-    const double e = fma(-x, r.y2, 1.0);
-    return fma(r.y3 * e, fma(1.875, e, 1.5), r.y3);
-}
+__device__ __forceinline__ double rsqrt(double x) { return rsqrt_pow<false>(x); }
+__device__ __forceinline__ double rsqrt_cubed(double x) { return rsqrt_pow<true>(x); }
 
 // FP64 -> FP32 from the bit fields (sign, exponent rebiased from 1023 to
 // 127, mantissa truncated to 23 bits) on the integer pipe: the hardware

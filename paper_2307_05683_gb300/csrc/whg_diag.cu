@@ -148,8 +148,8 @@ __global__ void k_kepler_sweep(const double* q, const double* v, const int* cfg,
 }
 
 // The same seeds refined with FP64 operations only (e = fma(-x, y, 1),
-// y^2 = y*y, y^3 = y^2*y): the references the integer-pipe forms in
-// whg_device.cuh must reproduce bit for bit.
+// y^2 = y*y, y^3 = y^2*y, the correction polynomial in FP64): references
+// the integer-pipe forms in whg_device.cuh must match within one ulp.
 __device__ double rcp_fp64_ref(double x)
 {
     const unsigned hi = (unsigned)__double2hiint(x);

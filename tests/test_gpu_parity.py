@@ -98,12 +98,14 @@ def test_own_rcp_rsqrt_against_cuda(whg):
     assert float(err.max()) <= 1.5
 
 
-def test_integer_pipe_refinement_matches_fp64_forms(whg):
-    """The reciprocal forms e = 1 - x y exactly on the integer pipe, and
-    x^(-1/2) and x^(-3/2) build y^2 and y^3 there: bit for bit the values of
-    the same refinements written with FP64 operations (fma(-x, y, 1), y*y,
-    y^2*y), over each routine's domain (1/x normal; x^(-3/2) normal) and
-    both signs for 1/x."""
+def test_integer_pipe_refinement_within_one_ulp_of_fp64_forms(whg):
+    """The reciprocal and the reciprocal square roots form their whole
+    correction (1 - x y and its square, or 1 - x y^2 and its square) on the
+    integer pipe, leaving one FP64 FMA: within one ulp of the same
+    refinements written with FP64 operations (fma(-x, y, 1), y*y, y^2*y)
+    over each routine's domain (1/x normal; x^(-3/2) normal) and both signs
+    for 1/x, equal to them for most arguments, and within 1.5 ulp (1/x: 1 ulp)
+    of the exact values."""
     import torch
     rng = np.random.default_rng(4)
     mag = 10.0 ** rng.uniform(-307, 307, 400000)
@@ -114,16 +116,23 @@ def test_integer_pipe_refinement_matches_fp64_forms(whg):
     out = torch.empty(10 * x.size, dtype=torch.float64, device="cuda")
     whg.whg_test_special(xt, out)
     r = out.cpu().numpy().reshape(10, -1)
+
+    def ulps(a, b):            # |a - b| in units of the double spacing at b
+        return np.abs(a - b) / np.spacing(np.abs(np.asarray(b, np.float64)))
+
     inv = np.abs(x) < 2.0 ** 1021                            # 1/x normal
-    assert inv.sum() > 500000 and np.array_equal(r[0][inv], r[6][inv])      # rcp
+    assert inv.sum() > 500000
+    assert ulps(r[0][inv], r[6][inv]).max() <= 1.0 and np.mean(r[0][inv] == r[6][inv]) > 0.9   # rcp
     pos = (x > 0) & (x < 4.0e307)
-    assert np.array_equal(r[2][pos], r[7][pos])              # rsqrt
+    assert ulps(r[2][pos], r[7][pos]).max() <= 1.0 and np.mean(r[2][pos] == r[7][pos]) > 0.9   # rsqrt
     cube = (x > 2.0 ** -680) & (x < 2.0 ** 681)               # x^(-3/2) normal
-    assert np.array_equal(r[8][cube], r[9][cube])            # x^(-3/2)
+    assert ulps(r[8][cube], r[9][cube]).max() <= 1.0 and np.mean(r[8][cube] == r[9][cube]) > 0.9
     sel = pos & (x > 1e-200) & (x < 1e200)
-    exact = np.asarray(x[sel], np.longdouble) ** np.longdouble(-1.5)
-    err = np.abs(r[8][sel].astype(np.longdouble) - exact) / np.spacing(np.abs(r[8][sel]))
-    assert float(err.max()) <= 2.0
+    xl = np.asarray(x[sel], np.longdouble)
+    assert float(ulps(r[8][sel].astype(np.longdouble), xl ** np.longdouble(-1.5)).max()) <= 1.5
+    assert float(ulps(r[2][sel].astype(np.longdouble), 1 / np.sqrt(xl)).max()) <= 1.5
+    sel = inv & (np.abs(x) > 1e-200) & (np.abs(x) < 1e200)
+    assert float(ulps(r[0][sel].astype(np.longdouble), 1 / np.asarray(x[sel], np.longdouble)).max()) <= 1.0
     # outside the domains the outcomes stay non-finite as in the FP64 forms: a
     # zero or subnormal argument gives the same infinite 1/x and x^(-3/2) (a
     # coincident pair of planets then freezes its system as non-finite), inf
