@@ -358,12 +358,13 @@ int whg_debug_bounds(whg_ctx* ctx, unsigned* flag);
 int whg_noalloc_debug_bounds(unsigned* flag);
 
 /* The library's own reciprocal, reciprocal square root and FP64 <-> FP32
- * conversions next to CUDA's, for testing: out [10][n] DEVICE buffer receives
+ * conversions next to CUDA's, for testing: out [12][n] DEVICE buffer receives
  * rcp_own(x), 1/x (CUDA, IEEE), rsqrt_own(x), rsqrt(x) (CUDA) (0 < x < 4e307
  * for the square roots, else 0), the own FP64 -> FP32 -> FP64 round trip of
  * x, CUDA's round-toward-zero FP64 -> FP32 conversion of x widened to FP64,
  * then the own routines' FP64-only reference forms: rcp, rsqrt, the own
- * x^(-3/2) and its reference (0 <= x < 4e307, else 0), for the n DEVICE
+ * x^(-3/2) and its reference (0 <= x < 4e307, else 0), then the own 1/x^2
+ * and the square of CUDA's 1/x (0 <= x < 4e307, else 0), for the n DEVICE
  * inputs x.
  * Blocks. */
 int whg_test_special(const double* x, int n, double* out);

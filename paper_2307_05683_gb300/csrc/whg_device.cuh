@@ -155,6 +155,35 @@ __device__ __forceinline__ double rcp(double x)
     return fma(y, t, y);
 }
 
+// 1/x^2 for finite x > 0 with 1/x^2 normal: the same seed, y^2 exact (48
+// bits) and 1/x^2 = y^2 (1 - e)^-2 = y^2 (1 + 2e + 3e^2 + ...), the
+// correction 2e + 3e^2 formed on the integer pipe as in rcp (the neglected
+// 4e^3 is below 2^-61).  1 FP64 operation instead of a reciprocal and a
+// square.  Zero and subnormal x give +inf, inf and NaN give NaN.
+__device__ __forceinline__ double rcp_sq(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    const int ex = (int)((hi >> 20) & 0x7ffu);                         // biased exponent
+    const float mant = __uint_as_float(0x3f800000u | ((hi & 0x000fffffu) << 3) | (lo >> 29));
+    const unsigned rb = __float_as_uint(approx_rcp_f32(mant));          // in (0.5, 1]
+    const int erb = (int)((rb >> 23) & 0xffu);
+    const int dex = erb - 127 + 2046 - ex;                              // biased exponent of 1/x
+    const unsigned long long My = (rb & 0x007fffffu) | 0x00800000u;
+    const unsigned long long S = My * My;                               // [2^46, 2^48), exact
+    const unsigned long long top = S >> 47;
+    const double y2 = exp_bits_to_double(2 * (long long)dex - 1023 + (long long)top,
+                                         (S << (6 - top)) & 0x000fffffffffffffULL);
+    const long long D = (long long)(0ULL - significand(hi, lo) * My);   // e 2^sc
+    const int sc = 202 - erb;                                           // 75..76
+    const long long Dh = D >> 24;
+    const long long T = 2 * D + 3 * ((Dh * Dh) >> ((sc - 48) & 63));   // (2e + 3e^2) 2^sc
+    double r = fma(y2, scaled_int_to_double(T, sc), y2);
+    r = ex == 0 ? __longlong_as_double(0x7ff0000000000000LL) : r;
+    r = ex == 0x7ff ? __longlong_as_double(0x7ff8000000000000LL) : r;
+    return r;
+}
+
 // x^(-1/2) and x^(-3/2) for finite normal x > 0 (x^(-3/2) normal for
 // 2^-681 < x < 2^682: the 1/r^3 of a pair from r^2), from the seed y of
 // rsqrt.approx on an FP32 copy of the mantissa (24-bit significand My, the
@@ -691,12 +720,12 @@ __device__ __forceinline__ bool kick(const Group<L>& g, double qx, double qy, do
     }
     if (GRM != 0) {
         // a_GR(Q) = -6 (G m0)^2 Q / (c^2 |Q|^4); kgr = -6 m0^2 dt / c^2.
-        const double ri2 = rcp(fma(qx, qx, fma(qy, qy, qz * qz)));
-        const double c = kgr * (ri2 * ri2);
+        const double r2 = fma(qx, qx, fma(qy, qy, qz * qz));
+        const double c = kgr * rcp_sq(r2);
         if constexpr (GEOM) {
             double* t = kt->p + (size_t)(4 * kKickTapeRound) * kt->NL;
             t[0] = c;
-            t[kt->NL] = 4.0 * c * ri2;
+            t[kt->NL] = 4.0 * c * rcp(r2);
             t[2 * kt->NL] = c * kt->two_muinv;
         }
         if (GRM == 1) {

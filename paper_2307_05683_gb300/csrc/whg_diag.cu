@@ -210,6 +210,9 @@ __global__ void k_special(const double* x, int n, double* out)
     const bool nonneg = v >= 0.0 && v < 4.0e307;      // also zero: a coincident pair's r^2
     out[8 * n + i] = nonneg ? whg::rsqrt_cubed(v) : 0.0;
     out[9 * n + i] = nonneg ? rsqrt_cubed_fp64_ref(v) : 0.0;
+    const double inv = 1.0 / v;
+    out[10 * n + i] = nonneg ? whg::rcp_sq(v) : 0.0;
+    out[11 * n + i] = nonneg ? inv * inv : 0.0;
 }
 
 }  // namespace

@@ -81,9 +81,9 @@ def test_own_rcp_rsqrt_against_cuda(whg):
                         10.0 ** rng.uniform(-6, 6, 200000),
                         1.0 + rng.uniform(-1e-9, 1e-9, 1000), [1.0, 2.0, 4.0, 0.5, 3.0]])
     xt = torch.tensor(x, dtype=torch.float64, device="cuda")
-    out = torch.empty(10 * x.size, dtype=torch.float64, device="cuda")
+    out = torch.empty(12 * x.size, dtype=torch.float64, device="cuda")
     whg.whg_test_special(xt, out)
-    r = out.cpu().numpy().reshape(10, -1)
+    r = out.cpu().numpy().reshape(12, -1)
     ulp_rcp = np.spacing(np.abs(r[1]))
     ulp_rsq = np.spacing(np.abs(r[3]))
     # CUDA's 1/x is correctly rounded; rsqrt is within 1 ulp of exact.
@@ -113,9 +113,9 @@ def test_integer_pipe_refinement_within_one_ulp_of_fp64_forms(whg):
                         np.nextafter(np.ldexp(1.0, np.arange(-1021, 1023)), np.inf),
                         1.0 + rng.uniform(-1e-7, 1e-7, 20000)])
     xt = torch.tensor(x, dtype=torch.float64, device="cuda")
-    out = torch.empty(10 * x.size, dtype=torch.float64, device="cuda")
+    out = torch.empty(12 * x.size, dtype=torch.float64, device="cuda")
     whg.whg_test_special(xt, out)
-    r = out.cpu().numpy().reshape(10, -1)
+    r = out.cpu().numpy().reshape(12, -1)
 
     def ulps(a, b):            # |a - b| in units of the double spacing at b
         return np.abs(a - b) / np.spacing(np.abs(np.asarray(b, np.float64)))
@@ -133,19 +133,24 @@ def test_integer_pipe_refinement_within_one_ulp_of_fp64_forms(whg):
     assert float(ulps(r[2][sel].astype(np.longdouble), 1 / np.sqrt(xl)).max()) <= 1.5
     sel = inv & (np.abs(x) > 1e-200) & (np.abs(x) < 1e200)
     assert float(ulps(r[0][sel].astype(np.longdouble), 1 / np.asarray(x[sel], np.longdouble)).max()) <= 1.0
+    # 1/x^2 (the GR term's factor) within 1.5 ulp of exact where it is normal
+    sq = (x > 1e-150) & (x < 1e150)
+    xq = np.asarray(x[sq], np.longdouble)
+    assert float(ulps(r[10][sq].astype(np.longdouble), 1 / (xq * xq)).max()) <= 1.5
     # outside the domains the outcomes stay non-finite as in the FP64 forms: a
     # zero or subnormal argument gives the same infinite 1/x and x^(-3/2) (a
     # coincident pair of planets then freezes its system as non-finite), inf
     # and NaN give NaN (the FP64 form gives some non-finite value)
     sp = np.array([0.0, -0.0, 5e-324, -1e-310, np.inf, -np.inf, np.nan])
     spt = torch.tensor(sp, dtype=torch.float64, device="cuda")
-    o = torch.empty(10 * sp.size, dtype=torch.float64, device="cuda")
+    o = torch.empty(12 * sp.size, dtype=torch.float64, device="cuda")
     whg.whg_test_special(spt, o)
-    q = o.cpu().numpy().reshape(10, -1)
+    q = o.cpu().numpy().reshape(12, -1)
     assert np.all(np.isinf(q[0][:4])) and np.array_equal(np.signbit(q[0][:4]), np.signbit(sp[:4]))
     assert np.all(np.isnan(q[0][4:]))
     assert np.array_equal(q[0][:4], q[6][:4]) and not np.any(np.isfinite(q[6][4:]))
     assert np.all(np.isinf(q[8][:3])) and np.array_equal(q[8][:3], q[9][:3])    # x^(-3/2) of 0, -0, 5e-324
+    assert np.all(np.isinf(q[10][:3]))                                         # 1/x^2 of 0, -0, 5e-324
 
 
 def test_own_fp32_conversions_against_cuda(whg):
@@ -162,9 +167,9 @@ def test_own_fp32_conversions_against_cuda(whg):
                         [0.0, -0.0, 1e-300, -1e-300, 1e300, -1e300, np.inf, -np.inf, np.nan,
                          float(np.finfo(np.float32).max), float(np.finfo(np.float32).tiny)]])
     xt = torch.tensor(x, dtype=torch.float64, device="cuda")
-    out = torch.empty(10 * x.size, dtype=torch.float64, device="cuda")
+    out = torch.empty(12 * x.size, dtype=torch.float64, device="cuda")
     whg.whg_test_special(xt, out)
-    r = out.cpu().numpy().reshape(10, -1)
+    r = out.cpu().numpy().reshape(12, -1)
     own, rz = r[4], r[5]
     ax = np.abs(x)
     normal = np.isfinite(x) & (ax >= 2.0 ** -126) & (ax < 2.0 ** 128)
