@@ -218,10 +218,12 @@ int whg_set_raw(whg_ctx* ctx, const double* Q, const double* v, const long long*
  * whg_init / whg_init_device and not stepped since.  Advances the state by
  * n_steps exactly as whg_step does (without repacking stopped systems, so
  * that every checkpoint has the same layout), keeping the state every
- * checkpoint_every steps in device memory owned by ctx: about
- * (n/K + 1) * 48 B + 3 * K * 592 B per planet lane (checkpoints and three
- * tape buffers).  target [S][N][3] and loss [S] are DEVICE pointers; target
- * is copied.  Async. */
+ * checkpoint_every steps in device memory owned by ctx (kept until
+ * whg_destroy): (n/K + 1) * 48 B per planet lane of checkpoints and
+ * K * 592 B per planet lane for each tape buffer (three, or with a tape
+ * budget of whg_adjoint_schedule up to one per segment; the per-step values
+ * of a segment that the backward half consumes).  target [S][N][3] and
+ * loss [S] are DEVICE pointers; target is copied.  Async. */
 int whg_adjoint_forward(whg_ctx* ctx, long long n_steps, int checkpoint_every, const double* target,
                         double* loss);
 
@@ -237,6 +239,38 @@ int whg_adjoint_forward(whg_ctx* ctx, long long n_steps, int checkpoint_every, c
  * with other weights.  Async. */
 int whg_adjoint_backward(whg_ctx* ctx, const double* loss_weight, double* grad_pos, double* grad_vel,
                          double* grad_mass);
+
+/* Scheduling of the adjoint; not part of the paper's method.  Results are
+ * bitwise the same under every setting.  Takes effect at the next
+ * whg_adjoint_forward.
+ * sm_split: -1 (default): split the SMs into two green contexts when the
+ *   ensemble's warps need at most half of the SMs at one warp per SM
+ *   sub-partition (about 1200 8-planet systems or fewer on a 152-SM GPU).
+ *   In the backward half the back kernels, its critical path, then run on
+ *   ceil(warps / 4) SMs (rounded up to the partition granularity, 8 SMs on
+ *   this GPU), one warp per sub-partition, and the tape kernels on the
+ *   remaining SMs, so that the two never share a sub-partition.
+ *   0: no split; the tape kernels run on two side streams beside the back
+ *   kernels, wherever the block scheduler puts them.
+ *   n > 0: split with n SMs for the back kernels.
+ *   Where green contexts are unavailable the adjoint runs unsplit.
+ * tape_bytes: tape buffers (K * 592 B per planet lane each, kept until
+ *   whg_destroy).  0 (default): three; each segment's tape is recomputed
+ *   during the backward half, two segments ahead of the back kernels.
+ *   With the split, a budget makes the tapes of the segments already passed
+ *   be recomputed during the forward half instead, beside it, into up to one
+ *   buffer per segment; the forward half then runs on the back kernels' SMs.
+ *   -1: as many buffers as fit in half of the free device memory at
+ *   whg_adjoint_forward; n > 0: at most n bytes (at least 3 buffers).
+ *   Segments without a buffer of their own get their tapes recomputed during
+ *   the backward half.
+ * Returns WHG_EINVAL for values below -1. */
+int whg_adjoint_schedule(whg_ctx* ctx, int sm_split, long long tape_bytes);
+
+/* After whg_adjoint_forward: SMs of the partition that runs the forward half
+ * and the back kernels and of the one that runs the tape kernels (both 0 when
+ * unsplit), and the number of tape buffers.  Any pointer may be NULL. */
+int whg_adjoint_layout(const whg_ctx* ctx, int* chain_sms, int* tape_sms, int* tape_buffers);
 
 /* Wait until all work issued on ctx's stream has finished. */
 int whg_synchronize(whg_ctx* ctx);

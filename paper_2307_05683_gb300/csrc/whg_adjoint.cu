@@ -10,9 +10,10 @@
 // products need, every part of them that does not depend on the adjoints
 // (pair separations and powers of 1/r, the GR factors, the Kepler drift's
 // coefficients), so that the back kernels, which run one after another and
-// form the critical path, do only the work linear in the adjoints.  The tapes
-// of segments s-1 and s-2 are recomputed on two side streams (three tape
-// buffers) while the products of segment s run.
+// form the critical path, do only the work linear in the adjoints.  The tape
+// kernels run beside them: on two side streams, segments s-1 and s-2 while the
+// products of segment s run, or, with the host's SM split, on SMs of their own
+// during the forward half (see whg_api.cu).
 //
 // VJPs, with lambda the adjoint of each quantity:
 //   J:  Q_i += c sum_j m_j v_j (c = (dt/2)/m0): lambda_v_j += c m_j Lambda,

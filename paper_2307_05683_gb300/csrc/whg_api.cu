@@ -13,6 +13,9 @@
 #include <new>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "whg_internal.h"
 
 struct whg_ctx {
@@ -38,7 +41,18 @@ struct whg_ctx {
     int adj_K, adj_nseg;
     bool adj_ready;
     cudaStream_t side[2];     // side streams for tape recomputation (created on first use)
-    cudaEvent_t ev_tape[WHG_TAPE_BUFFERS], ev_back[WHG_TAPE_BUFFERS], ev_entry;
+    cudaEvent_t ev_entry, ev_ckpt, ev_exit;
+    std::vector<cudaEvent_t> ev_tape, ev_back;   // per tape buffer
+    std::vector<int> tape_of; // segment whose tape each buffer holds (-1: none)
+    int adj_nbuf;             // tape buffers of the current forward half
+    // adjoint scheduling (whg_adjoint_schedule): SM split by green contexts
+    int cfg_split;            // -1 auto, 0 off, n > 0: SMs of the chain partition
+    long long cfg_tape_bytes; // 0 three buffers (default), -1 half the free memory, n > 0 cap
+    bool split;               // the current forward half runs split
+    int chain_sms, tape_sms;  // SMs of the two green contexts (0: none)
+    CUgreenCtx g_chain, g_tape;
+    CUcontext x_chain, x_tape;
+    cudaStream_t s_chain, s_tape[2];
     // CUDA graph of graph_launches step launches of graph_chunk steps each
     cudaStream_t capture;
     cudaGraphExec_t graph;
@@ -343,6 +357,8 @@ int whg_create(whg_ctx** out, int n_systems, int max_planets, const whg_options*
     c->warps_cap = warps_capacity(n_systems, max_planets, Lfixed);
     c->opt = opt;
     c->stream = (cudaStream_t)cuda_stream;
+    c->cfg_split = -1;
+    c->cfg_tape_bytes = 0;
     cudaError_t e = cudaGetDevice(&c->device);
     if (e != cudaSuccess) {
         delete c;
@@ -512,7 +528,9 @@ int whg_init_device(whg_ctx* c, const double* masses, const double* pos, const d
 
 // n steps; repack = false (the adjoint's forward half) keeps every system on
 // its lanes: no repack, and no replay of a captured graph that holds one.
-static int step_impl(whg_ctx* c, long long n, bool repack)
+// `over` (the adjoint's partition) replaces the launch configuration and
+// skips graphs.
+static int step_impl(whg_ctx* c, long long n, bool repack, const WhgLaunch* over = nullptr)
 {
     long long chunk = c->opt.steps_per_launch;
     if (chunk <= 0) {
@@ -520,11 +538,11 @@ static int step_impl(whg_ctx* c, long long n, bool repack)
         chunk = 50000000LL / ((long long)c->bk.warp0[c->bk.nb] * 4 + 1);
         if (chunk < 1) chunk = 1;
     }
-    WhgLaunch l = launch_cfg(c);
+    WhgLaunch l = over ? *over : launch_cfg(c);
     if (c->host_nstep >= 0) c->host_nstep += n;
     c->adj_ready = false;
     const long long G = c->opt.graph_launches;
-    if (G > 0 && n >= G * chunk && (repack || !c->repack_buf)) {
+    if (!over && G > 0 && n >= G * chunk && (repack || !c->repack_buf)) {
         if (!c->graph || c->graph_chunk != chunk) {      // capture G launches once
             if (c->graph) {
                 cudaGraphExecDestroy(c->graph);
@@ -729,21 +747,172 @@ int whg_test_queue_timeout(whg_ctx* c, long long spin_limit, int* flag)
 
 const char* whg_last_error(const whg_ctx* c) { return c ? c->err : g_create_err; }
 
+}  // extern "C"
+
+namespace {
+
+// ---- adjoint scheduling ------------------------------------------------------
+//
+// The back kernels of consecutive segments form the adjoint's critical path,
+// and at the ensemble sizes where the gradient is wanted (about a thousand
+// systems) each of their warps runs alone on an SM sub-partition, at the rate
+// one warp's dependency chains allow.  The tape kernels' warps, placed by the
+// block scheduler on the same sub-partitions, halve that rate.  So, where the
+// ensemble's warps fill at most half of the GPU at one warp per sub-partition,
+// the SMs are split in two green contexts for the backward half: the back
+// kernels run on the first (4 warps per block: one per sub-partition), the
+// tape kernels on the second, and the two never share an SM.  Optionally
+// (a tape budget) the tapes of the segments already passed are recomputed
+// during the forward half instead, into a pool of buffers; the forward half
+// then runs on the first partition too.  That measured no faster at a
+// thousand systems (the tape partition keeps up with the back kernels either
+// way, and the forward half loses a little on fewer SMs), so it is off by
+// default.  Results are bitwise the same under every schedule: every
+// kernel's arithmetic is per warp.
+
+// Driver entry points for green contexts, fetched through the runtime so that
+// the library does not link the driver library.
+struct GreenApi {
+    PFN_cuDeviceGetDevResource_v12040 get_resource = nullptr;
+    PFN_cuDevSmResourceSplitByCount_v12040 split = nullptr;
+    PFN_cuDevResourceGenerateDesc_v12040 make_desc = nullptr;
+    PFN_cuGreenCtxCreate_v12040 create = nullptr;
+    PFN_cuGreenCtxDestroy_v12040 destroy = nullptr;
+    PFN_cuCtxFromGreenCtx_v12040 as_ctx = nullptr;
+    PFN_cuGreenCtxStreamCreate_v12050 stream_create = nullptr;
+    PFN_cuStreamDestroy_v4000 stream_destroy = nullptr;
+    PFN_cuCtxPushCurrent_v4000 push = nullptr;
+    PFN_cuCtxPopCurrent_v4000 pop = nullptr;
+    bool ok = false;
+};
+
+template <class F>
+static bool driver_fn(const char* name, unsigned version, F* out)
+{
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    void* p = nullptr;
+    const cudaError_t e = cudaGetDriverEntryPointByVersion(name, &p, version, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p) {
+        cudaGetLastError();
+        return false;
+    }
+    *out = reinterpret_cast<F>(p);
+    return true;
+}
+
+static const GreenApi& green_api()
+{
+    static const GreenApi api = [] {
+        GreenApi a;
+        a.ok = driver_fn("cuDeviceGetDevResource", 12040, &a.get_resource) &&
+               driver_fn("cuDevSmResourceSplitByCount", 12040, &a.split) &&
+               driver_fn("cuDevResourceGenerateDesc", 12040, &a.make_desc) &&
+               driver_fn("cuGreenCtxCreate", 12040, &a.create) &&
+               driver_fn("cuGreenCtxDestroy", 12040, &a.destroy) &&
+               driver_fn("cuCtxFromGreenCtx", 12040, &a.as_ctx) &&
+               driver_fn("cuGreenCtxStreamCreate", 12050, &a.stream_create) &&
+               driver_fn("cuStreamDestroy", 4000, &a.stream_destroy) &&
+               driver_fn("cuCtxPushCurrent", 4000, &a.push) && driver_fn("cuCtxPopCurrent", 4000, &a.pop);
+        return a;
+    }();
+    return api;
+}
+
+// Makes a green context current while work is issued into its streams (the
+// runtime launches into the current context); a null context does nothing.
+struct CtxScope {
+    CUcontext ctx;
+    bool ok;
+    explicit CtxScope(CUcontext x) : ctx(x), ok(true)
+    {
+        if (ctx) ok = green_api().push(ctx) == CUDA_SUCCESS;
+    }
+    ~CtxScope()
+    {
+        CUcontext prev;
+        if (ctx && ok) green_api().pop(&prev);
+    }
+};
+
+#define WHG_SCOPE(ctx_, x)                                                              \
+    CtxScope scope_##x(ctx_);                                                           \
+    if (!scope_##x.ok) return fail(c, WHG_ECUDA, "cuCtxPushCurrent of a green context failed")
+
+static void release_split(whg_ctx* c)
+{
+    const GreenApi& g = green_api();
+    if (c->s_chain) g.stream_destroy((CUstream)c->s_chain);
+    for (int i = 0; i < 2; ++i)
+        if (c->s_tape[i]) g.stream_destroy((CUstream)c->s_tape[i]);
+    if (c->g_chain) g.destroy(c->g_chain);
+    if (c->g_tape) g.destroy(c->g_tape);
+    c->s_chain = c->s_tape[0] = c->s_tape[1] = nullptr;
+    c->g_chain = c->g_tape = nullptr;
+    c->x_chain = c->x_tape = nullptr;
+    c->chain_sms = c->tape_sms = 0;
+}
+
+// Green contexts of `want` SMs (rounded up to the partition granularity) and
+// of the rest, with one stream in the first and two in the second.  Returns
+// false, with no partition, where that is not possible.
+static bool make_split(whg_ctx* c, int want)
+{
+    const GreenApi& g = green_api();
+    if (!g.ok) return false;
+    if (c->g_chain && c->chain_sms >= want && c->chain_sms < want + 8) return true;
+    release_split(c);
+    CUdevResource all{}, part{}, rest{};
+    if (g.get_resource((CUdevice)c->device, &all, CU_DEV_RESOURCE_TYPE_SM) != CUDA_SUCCESS) return false;
+    unsigned n = 1;
+    if (g.split(&part, &n, &all, &rest, 0, (unsigned)want) != CUDA_SUCCESS || n != 1 ||
+        rest.sm.smCount < 8)
+        return false;
+    CUdevResourceDesc dc = nullptr, dt = nullptr;
+    bool ok = g.make_desc(&dc, &part, 1) == CUDA_SUCCESS && g.make_desc(&dt, &rest, 1) == CUDA_SUCCESS &&
+              g.create(&c->g_chain, dc, (CUdevice)c->device, CU_GREEN_CTX_DEFAULT_STREAM) == CUDA_SUCCESS &&
+              g.create(&c->g_tape, dt, (CUdevice)c->device, CU_GREEN_CTX_DEFAULT_STREAM) == CUDA_SUCCESS &&
+              g.as_ctx(&c->x_chain, c->g_chain) == CUDA_SUCCESS && g.as_ctx(&c->x_tape, c->g_tape) == CUDA_SUCCESS;
+    CUstream s0 = nullptr, s1 = nullptr, s2 = nullptr;
+    ok = ok && g.stream_create(&s0, c->g_chain, CU_STREAM_NON_BLOCKING, 0) == CUDA_SUCCESS;
+    c->s_chain = (cudaStream_t)s0;
+    ok = ok && g.stream_create(&s1, c->g_tape, CU_STREAM_NON_BLOCKING, 0) == CUDA_SUCCESS;
+    c->s_tape[0] = (cudaStream_t)s1;
+    ok = ok && g.stream_create(&s2, c->g_tape, CU_STREAM_NON_BLOCKING, 0) == CUDA_SUCCESS;
+    c->s_tape[1] = (cudaStream_t)s2;
+    if (!ok) {
+        release_split(c);
+        return false;
+    }
+    c->chain_sms = (int)part.sm.smCount;
+    c->tape_sms = (int)rest.sm.smCount;
+    return true;
+}
+
 // Side streams and events of the adjoint (created on first use).
 static int adjoint_streams(whg_ctx* c)
 {
     if (c->side[0]) return WHG_OK;
     for (int i = 0; i < 2; ++i) WHG_CUDA(c, cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking));
-    for (int i = 0; i < WHG_TAPE_BUFFERS; ++i) {
-        WHG_CUDA(c, cudaEventCreateWithFlags(&c->ev_tape[i], cudaEventDisableTiming));
-        WHG_CUDA(c, cudaEventCreateWithFlags(&c->ev_back[i], cudaEventDisableTiming));
-    }
     WHG_CUDA(c, cudaEventCreateWithFlags(&c->ev_entry, cudaEventDisableTiming));
+    WHG_CUDA(c, cudaEventCreateWithFlags(&c->ev_ckpt, cudaEventDisableTiming));
+    WHG_CUDA(c, cudaEventCreateWithFlags(&c->ev_exit, cudaEventDisableTiming));
     return WHG_OK;
 }
 
-// Tape buffer of segment j (WHG_TAPE_BUFFERS rotating buffers).
-static int tape_buffer(int j) { return j % WHG_TAPE_BUFFERS; }
+// nbuf tape buffers' events and bookkeeping (no segment held).
+static int tape_pool(whg_ctx* c, int nbuf)
+{
+    while ((int)c->ev_tape.size() < nbuf) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        WHG_CUDA(c, cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+        c->ev_tape.push_back(a);
+        WHG_CUDA(c, cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
+        c->ev_back.push_back(b);
+    }
+    c->tape_of.assign((size_t)nbuf, -1);
+    c->adj_nbuf = nbuf;
+    return WHG_OK;
+}
 
 static int segment_length(const whg_ctx* c, int seg)
 {
@@ -751,13 +920,97 @@ static int segment_length(const whg_ctx* c, int seg)
     return (int)(s0 + c->adj_K <= c->adj_n ? c->adj_K : c->adj_n - s0);
 }
 
-static int launch_tape(whg_ctx* c, const WhgAdj& a, int j, cudaStream_t stream)
+// Launch shapes: the chain (forward steps, checkpoints, loss, back kernels;
+// on the first partition when `on_split`) and the tape kernels.
+static WhgLaunch chain_cfg(const whg_ctx* c, bool on_split)
 {
     WhgLaunch l = launch_cfg(c);
-    l.stream = stream;
-    return launch_check(c, whg_launch_adj_tape(c->st, c->bk, a, j, (long long)j * c->adj_K, segment_length(c, j),
-                                               tape_buffer(j), c->opt.newton_terms, c->opt.gr_mode, l),
-                        "adjoint tape kernel");
+    if (on_split) {
+        const long long threads = (long long)c->bk.warp0[c->bk.nb] * 32;
+        l.block = 128;
+        l.grid = (int)((threads + 127) / 128);
+        if (l.grid < 1) l.grid = 1;
+        l.stream = c->s_chain;
+    }
+    return l;
+}
+
+static WhgLaunch tape_cfg(const whg_ctx* c, int i)
+{
+    WhgLaunch l = launch_cfg(c);
+    l.stream = c->split ? c->s_tape[i] : c->side[i];
+    return l;
+}
+
+static int launch_tape(whg_ctx* c, const WhgAdj& a, int j, int i)
+{
+    const int b = j % c->adj_nbuf;
+    const int rc = launch_check(c, whg_launch_adj_tape(c->st, c->bk, a, j, (long long)j * c->adj_K,
+                                                       segment_length(c, j), b, c->opt.newton_terms,
+                                                       c->opt.gr_mode, tape_cfg(c, i)),
+                                "adjoint tape kernel");
+    if (rc) return rc;
+    c->tape_of[(size_t)b] = j;
+    WHG_CUDA(c, cudaEventRecord(c->ev_tape[(size_t)b], tape_cfg(c, i).stream));
+    return WHG_OK;
+}
+
+// Work issued on the context's stream so far comes before `s`.
+static int enter_stream(whg_ctx* c, cudaStream_t s, CUcontext x)
+{
+    WHG_SCOPE(x, enter);
+    WHG_CUDA(c, cudaStreamWaitEvent(s, c->ev_entry, 0));
+    return WHG_OK;
+}
+
+// The context's stream waits for the work issued on `s`.
+static int leave_stream(whg_ctx* c, cudaStream_t s, CUcontext x)
+{
+    {
+        WHG_SCOPE(x, leave);
+        WHG_CUDA(c, cudaEventRecord(c->ev_exit, s));
+    }
+    WHG_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_exit, 0));
+    return WHG_OK;
+}
+
+// SMs wanted for the chain partition (0: no split) for this ensemble.
+static int chain_sms_wanted(const whg_ctx* c)
+{
+    if (c->cfg_split == 0) return 0;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int warps = c->bk.warp0[c->bk.nb];
+    const int want = c->cfg_split > 0 ? c->cfg_split : (warps + 3) / 4;   // one warp per sub-partition
+    if (c->cfg_split < 0 && 2 * want > sms) return 0;                      // the forward fills the GPU
+    if (want >= sms) return 0;
+    return want;
+}
+
+}  // namespace
+
+extern "C" {
+
+int whg_adjoint_schedule(whg_ctx* c, int sm_split, long long tape_bytes)
+{
+    if (!c) return WHG_EINVAL;
+    if (sm_split < -1 || tape_bytes < -1)
+        return fail(c, WHG_EINVAL, "sm_split=%d and tape_bytes=%lld must be >= -1", sm_split, tape_bytes);
+    c->cfg_split = sm_split;
+    c->cfg_tape_bytes = tape_bytes;
+    return WHG_OK;
+}
+
+int whg_adjoint_layout(const whg_ctx* c, int* chain_sms, int* tape_sms, int* tape_buffers)
+{
+    if (!c) return WHG_EINVAL;
+    if (chain_sms) *chain_sms = c->split ? c->chain_sms : 0;
+    if (tape_sms) *tape_sms = c->split ? c->tape_sms : 0;
+    if (tape_buffers) *tape_buffers = c->adj_nbuf;
+    return WHG_OK;
 }
 
 int whg_adjoint_forward(whg_ctx* c, long long n_steps, int checkpoint_every, const double* target,
@@ -769,15 +1022,41 @@ int whg_adjoint_forward(whg_ctx* c, long long n_steps, int checkpoint_every, con
     if (n_steps < 0 || checkpoint_every < 1)
         return fail(c, WHG_EINVAL, "need n_steps >= 0 and checkpoint_every >= 1");
     if (!target || !loss) return fail(c, WHG_EINVAL, "null target or loss");
+    int rc = adjoint_streams(c);
+    if (rc) return rc;
     const size_t NL = (size_t)c->bk.warp0[c->bk.nb] * 32;
     const long long nseg = (n_steps + checkpoint_every - 1) / checkpoint_every;
     const int K = (int)(n_steps < checkpoint_every ? (n_steps > 0 ? n_steps : 1) : checkpoint_every);
     const size_t tgt = (size_t)c->S * c->Nmax * 3;
     const size_t tape_len = (size_t)K * WHG_TAPE_W * NL;
-    const size_t nd = (size_t)(nseg + 1) * 6 * NL + WHG_TAPE_BUFFERS * tape_len + 8 * NL + tgt;
-    const size_t bytes = nd * sizeof(double);
-    if (bytes > c->adj_bytes) {
-        if (c->adj_buf) cudaFree(c->adj_buf);
+    const size_t fixed = ((size_t)(nseg + 1) * 6 * NL + 8 * NL + tgt) * sizeof(double);
+    const size_t tape_bytes = tape_len * sizeof(double);
+    // the partition, then the tape pool: with the split and a tape budget, a
+    // buffer per segment where they fit (half of the free memory, or the cap)
+    const int want = chain_sms_wanted(c);
+    c->split = want > 0 && make_split(c, want);
+    const bool pre = c->split && c->cfg_tape_bytes != 0;   // tapes beside the forward half
+    long long nbuf = WHG_TAPE_BUFFERS;
+    if (pre) {
+        size_t cap = 0;
+        if (c->cfg_tape_bytes > 0) {
+            cap = (size_t)c->cfg_tape_bytes;
+        } else {
+            size_t free_b = 0, total_b = 0;
+            WHG_CUDA(c, cudaMemGetInfo(&free_b, &total_b));
+            cap = (free_b + (c->adj_buf ? c->adj_bytes : 0)) / 2;
+            cap = cap > fixed ? cap - fixed : 0;
+        }
+        const long long fit = (long long)(cap / tape_bytes);
+        nbuf = fit < nseg ? fit : nseg;
+        if (nbuf < WHG_TAPE_BUFFERS) nbuf = WHG_TAPE_BUFFERS;
+    }
+    const size_t bytes = fixed + (size_t)nbuf * tape_bytes;
+    if (bytes > c->adj_bytes || (c->adj_bytes > 2 * bytes && c->adj_bytes - bytes > ((size_t)1 << 30))) {
+        if (c->adj_buf) {
+            WHG_CUDA(c, cudaStreamSynchronize(c->stream));
+            cudaFree(c->adj_buf);
+        }
         c->adj_buf = nullptr;
         c->adj_bytes = 0;
         cudaError_t e = cudaMalloc(&c->adj_buf, bytes);
@@ -785,13 +1064,15 @@ int whg_adjoint_forward(whg_ctx* c, long long n_steps, int checkpoint_every, con
                                           cudaGetErrorString(e));
         c->adj_bytes = bytes;
     }
+    rc = tape_pool(c, (int)nbuf);
+    if (rc) return rc;
     WhgAdj& a = c->adj;
     a = WhgAdj{};
     a.NL = NL;
     a.ckpt = c->adj_buf;
     a.tape = a.ckpt + (size_t)(nseg + 1) * 6 * NL;
     a.tape_len = tape_len;
-    a.lam = a.tape + WHG_TAPE_BUFFERS * tape_len;
+    a.lam = a.tape + (size_t)nbuf * tape_len;
     double* tcopy = a.lam + 8 * NL;
     a.target = tcopy;
     c->adj_n = n_steps;
@@ -799,22 +1080,60 @@ int whg_adjoint_forward(whg_ctx* c, long long n_steps, int checkpoint_every, con
     c->adj_nseg = (int)nseg;
     c->adj_ready = false;
     WHG_CUDA(c, cudaMemcpyAsync(tcopy, target, tgt * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    int rc = adjoint_streams(c);
-    if (rc) return rc;
-    const WhgLaunch l = launch_cfg(c);
-    for (long long seg = 0; seg < nseg; ++seg) {
-        rc = launch_check(c, whg_launch_adj_save(c->st, c->bk, a, (int)seg, l), "checkpoint kernel");
-        if (rc) return rc;
+    // Segments whose tapes are recomputed beside the forward half: with a tape
+    // budget all that have a buffer, else (split) the last nbuf - 1, which the
+    // first back kernels need at once.  From segment `from` on, the forward
+    // runs on the first partition, so that no tape kernel shares its SMs.
+    const long long npre = !c->split ? 0 : pre ? (nbuf < nseg ? nbuf : nseg)
+                                                : (nbuf - 1 < nseg ? nbuf - 1 : nseg);
+    const long long first_pre = nseg - npre, from = pre ? 0 : first_pre;
+    const CUcontext xt = c->split ? c->x_tape : nullptr;
+    WhgLaunch l = chain_cfg(c, false);
+    CUcontext xc = nullptr;
+    bool switched = false;
+    for (long long seg = 0; seg <= nseg; ++seg) {
+        if (c->split && seg == from) {                  // onto the partition
+            WHG_CUDA(c, cudaEventRecord(c->ev_entry, c->stream));
+            for (cudaStream_t s : {c->s_chain, c->s_tape[0], c->s_tape[1]}) {
+                rc = enter_stream(c, s, s == c->s_chain ? c->x_chain : xt);
+                if (rc) return rc;
+            }
+            l = chain_cfg(c, true);
+            xc = c->x_chain;
+            switched = true;
+        }
+        {
+            WHG_SCOPE(xc, save);
+            rc = launch_check(c, whg_launch_adj_save(c->st, c->bk, a, (int)seg, l), "checkpoint kernel");
+            if (rc) return rc;
+            if (seg >= first_pre && seg < nseg) WHG_CUDA(c, cudaEventRecord(c->ev_ckpt, l.stream));
+        }
+        if (seg == nseg) break;
+        if (seg >= first_pre) {
+            WHG_SCOPE(xt, tape);
+            const int i = (int)(seg % 2);
+            WHG_CUDA(c, cudaStreamWaitEvent(c->s_tape[i], c->ev_ckpt, 0));
+            rc = launch_tape(c, a, (int)seg, i);
+            if (rc) return rc;
+        }
         const long long k = (seg + 1) * checkpoint_every <= n_steps ? checkpoint_every
                                                                      : n_steps - seg * checkpoint_every;
-        rc = step_impl(c, k, false);
+        WHG_SCOPE(xc, steps);
+        rc = step_impl(c, k, false, switched ? &l : nullptr);
         if (rc) return rc;
     }
-    rc = launch_check(c, whg_launch_adj_save(c->st, c->bk, a, (int)nseg, l), "checkpoint kernel");
-    if (rc) return rc;
-    a.loss = loss;
-    rc = launch_check(c, whg_launch_adj_loss(c->st, c->bk, a, 0, c->opt.newton_terms, l), "loss kernel");
-    if (rc) return rc;
+    {
+        WHG_SCOPE(xc, last);
+        a.loss = loss;
+        rc = launch_check(c, whg_launch_adj_loss(c->st, c->bk, a, 0, c->opt.newton_terms, l), "loss kernel");
+        if (rc) return rc;
+    }
+    if (switched) {
+        for (cudaStream_t s : {c->s_chain, c->s_tape[0], c->s_tape[1]}) {
+            rc = leave_stream(c, s, s == c->s_chain ? c->x_chain : xt);
+            if (rc) return rc;
+        }
+    }
     c->adj_ready = true;
     return WHG_OK;
 }
@@ -831,54 +1150,97 @@ int whg_adjoint_backward(whg_ctx* c, const double* loss_weight, double* grad_pos
     a.gu = grad_vel;
     a.gm = grad_mass;
     a.loss = nullptr;
-    const WhgLaunch l = launch_cfg(c);
-    int rc = launch_check(c, whg_launch_adj_loss(c->st, c->bk, a, 1, c->opt.newton_terms, l), "adjoint start");
+    int rc = adjoint_streams(c);
     if (rc) return rc;
-    rc = adjoint_streams(c);
-    if (rc) return rc;
-    // the side streams start after everything issued so far (checkpoints,
-    // adjoint start)
+    const WhgLaunch l = chain_cfg(c, c->split);
+    const CUcontext xc = c->split ? c->x_chain : nullptr, xt = c->split ? c->x_tape : nullptr;
+    const cudaStream_t ts[2] = {tape_cfg(c, 0).stream, tape_cfg(c, 1).stream};
+    // every stream starts after everything issued so far (checkpoints, tapes
+    // of the forward half, earlier backward halves)
     WHG_CUDA(c, cudaEventRecord(c->ev_entry, c->stream));
-    for (int i = 0; i < 2; ++i) WHG_CUDA(c, cudaStreamWaitEvent(c->side[i], c->ev_entry, 0));
-    // The products of segment s run on the context's stream (the critical
-    // path) while the tapes of segments s-1 and s-2 are recomputed on the two
-    // side streams: tape j into buffer j % 3 once the products of segment
-    // j + 3 are done with it.
-    const int nseg = c->adj_nseg;
-    if (nseg > 0) {
-        rc = launch_tape(c, a, nseg - 1, c->stream);
+    if (c->split) {
+        rc = enter_stream(c, l.stream, xc);
         if (rc) return rc;
     }
-    if (nseg > 1) {
-        rc = launch_tape(c, a, nseg - 2, c->side[(nseg - 2) % 2]);
+    for (int i = 0; i < 2; ++i) {
+        rc = enter_stream(c, ts[i], xt);
         if (rc) return rc;
-        WHG_CUDA(c, cudaEventRecord(c->ev_tape[tape_buffer(nseg - 2)], c->side[(nseg - 2) % 2]));
+    }
+    {
+        WHG_SCOPE(xc, start);
+        rc = launch_check(c, whg_launch_adj_loss(c->st, c->bk, a, 1, c->opt.newton_terms, l), "adjoint start");
+        if (rc) return rc;
+    }
+    // The products of segment s run on the chain stream (the critical path).
+    // Segment j's tape lives in buffer j % nbuf; a tape not already there is
+    // recomputed on a tape stream nbuf - 1 segments ahead, once the products
+    // of segment j + nbuf are done with the buffer.
+    const int nseg = c->adj_nseg, nbuf = c->adj_nbuf;
+    std::vector<char> fresh((size_t)nbuf, 0);
+    auto need_tape = [&](int j, bool after_back) -> int {
+        const int b = j % nbuf;
+        if (c->tape_of[(size_t)b] == j) return WHG_OK;
+        WHG_SCOPE(xt, tape);
+        const int i = j % 2;
+        if (after_back && j + nbuf <= nseg - 1) WHG_CUDA(c, cudaStreamWaitEvent(ts[i], c->ev_back[(size_t)b], 0));
+        const int r = launch_tape(c, a, j, i);
+        if (r) return r;
+        fresh[(size_t)b] = 1;
+        return WHG_OK;
+    };
+    for (int j = nseg - 1; j >= 0 && j > nseg - nbuf; --j) {
+        rc = need_tape(j, false);
+        if (rc) return rc;
     }
     for (int seg = nseg - 1; seg >= 0; --seg) {
-        const int j = seg - 2;
+        const int j = seg - (nbuf - 1);
         if (j >= 0) {
-            cudaStream_t side = c->side[j % 2];
-            if (j + WHG_TAPE_BUFFERS <= nseg - 1)
-                WHG_CUDA(c, cudaStreamWaitEvent(side, c->ev_back[tape_buffer(j)], 0));
-            rc = launch_tape(c, a, j, side);
+            rc = need_tape(j, true);
             if (rc) return rc;
-            WHG_CUDA(c, cudaEventRecord(c->ev_tape[tape_buffer(j)], side));
         }
-        if (seg < nseg - 1) WHG_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_tape[tape_buffer(seg)], 0));
+        const int b = seg % nbuf;
+        WHG_SCOPE(xc, back);
+        if (fresh[(size_t)b]) WHG_CUDA(c, cudaStreamWaitEvent(l.stream, c->ev_tape[(size_t)b], 0));
+        fresh[(size_t)b] = 0;
         rc = launch_check(c, whg_launch_adj_back(c->st, c->bk, a, (long long)seg * c->adj_K,
-                                                 segment_length(c, seg), tape_buffer(seg),
-                                                 c->opt.newton_terms, c->opt.gr_mode, l),
+                                                 segment_length(c, seg), b, c->opt.newton_terms,
+                                                 c->opt.gr_mode, l),
                           "adjoint back kernel");
         if (rc) return rc;
-        WHG_CUDA(c, cudaEventRecord(c->ev_back[tape_buffer(seg)], c->stream));
+        WHG_CUDA(c, cudaEventRecord(c->ev_back[(size_t)b], l.stream));
     }
-    return launch_check(c, whg_launch_adj_finish(c->st, c->bk, a, l), "adjoint finish kernel");
+    {
+        WHG_SCOPE(xc, finish);
+        rc = launch_check(c, whg_launch_adj_finish(c->st, c->bk, a, l), "adjoint finish kernel");
+        if (rc) return rc;
+    }
+    if (c->split) {
+        rc = leave_stream(c, l.stream, xc);
+        if (rc) return rc;
+    }
+    for (int i = 0; i < 2; ++i) {
+        rc = leave_stream(c, ts[i], xt);
+        if (rc) return rc;
+    }
+    return WHG_OK;
 }
 
 void whg_destroy(whg_ctx* c)
 {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    if (c->g_chain) {
+        {
+            CtxScope sc(c->x_chain);
+            if (sc.ok) cudaStreamSynchronize(c->s_chain);
+        }
+        {
+            CtxScope sc(c->x_tape);
+            if (sc.ok)
+                for (int i = 0; i < 2; ++i) cudaStreamSynchronize(c->s_tape[i]);
+        }
+        release_split(c);
+    }
     cudaFree(c->st.m);
     cudaFree(c->stage_d);
     if (c->repack_buf) cudaFree(c->repack_buf);
@@ -887,11 +1249,13 @@ void whg_destroy(whg_ctx* c)
     if (c->adj_buf) cudaFree(c->adj_buf);
     if (c->side[0]) {
         for (int i = 0; i < 2; ++i) cudaStreamSynchronize(c->side[i]);
-        for (int i = 0; i < WHG_TAPE_BUFFERS; ++i) {
+        for (size_t i = 0; i < c->ev_tape.size(); ++i) {
             cudaEventDestroy(c->ev_tape[i]);
             cudaEventDestroy(c->ev_back[i]);
         }
         cudaEventDestroy(c->ev_entry);
+        cudaEventDestroy(c->ev_ckpt);
+        cudaEventDestroy(c->ev_exit);
         for (int i = 0; i < 2; ++i) cudaStreamDestroy(c->side[i]);
     }
     if (c->graph) cudaGraphExecDestroy(c->graph);

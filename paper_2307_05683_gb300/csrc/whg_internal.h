@@ -105,13 +105,14 @@ struct WhgOut {
 // Buffers of the adjoint (reverse-mode) pass; NL = lanes of the layout.
 // Doubles per lane and step on the adjoint's tape (layout in whg_adjoint.cu).
 #define WHG_TAPE_W 74
-// Tape buffers: segments s-1 and s-2 are recomputed while the products of
-// segment s run.
+// Tape buffers at least (and without the SM split): segments s-1 and s-2 are
+// recomputed while the products of segment s run.  Segment j uses buffer
+// j mod (number of buffers).
 #define WHG_TAPE_BUFFERS 3
 
 struct WhgAdj {
     double* ckpt;                    // [nseg + 1][6][NL] state every K steps
-    double* tape;                    // [WHG_TAPE_BUFFERS][K][WHG_TAPE_W][NL] per-step values of a segment
+    double* tape;                    // [buffers][K][WHG_TAPE_W][NL] per-step values of a segment
     size_t tape_len;                 // K * WHG_TAPE_W * NL (one buffer)
     double* lam;                     // [8][NL] adjoints: Q (3), v (3), m, m0 (partial)
     const double* target;            // [S][Nmax][3] caller order

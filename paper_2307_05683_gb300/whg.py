@@ -90,6 +90,9 @@ def load():
                                                 ctypes.c_longlong, D, D]),
             "whg_adjoint_forward": (ctypes.c_int, [P, ctypes.c_longlong, ctypes.c_int, D, D]),
             "whg_adjoint_backward": (ctypes.c_int, [P, D, D, D, D]),
+            "whg_adjoint_schedule": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_longlong]),
+            "whg_adjoint_layout": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                                  ctypes.POINTER(ctypes.c_int)]),
             "whg_integrate_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int,
                                                      ctypes.POINTER(whg_options), D, D, D, I, D,
                                                      ctypes.c_longlong, D, D, I, D, ctypes.c_void_p]),
@@ -110,7 +113,8 @@ def exported_symbols() -> list[str]:
             "whg_launch_count", "whg_last_error", "whg_destroy", "whg_measure_fp64_tflops",
             "whg_test_special", "whg_integrate_noalloc", "whg_adjoint_forward",
             "whg_adjoint_backward", "whg_kepler_sweep", "whg_probe_fp64_lanes", "whg_test_queue_timeout",
-            "whg_debug_bounds", "whg_noalloc_debug_bounds", "whg_probe_fp64_kind"]
+            "whg_debug_bounds", "whg_noalloc_debug_bounds", "whg_probe_fp64_kind",
+            "whg_adjoint_schedule", "whg_adjoint_layout"]
 
 
 def _check(ctx, rc: int) -> None:
@@ -237,6 +241,16 @@ def whg_adjoint_backward(ctx, loss_weight, grad_pos, grad_vel, grad_mass) -> Non
     _check(ctx, load().whg_adjoint_backward(ctx, _dev(loss_weight, "torch.float64"),
                                             _dev(grad_pos, "torch.float64"), _dev(grad_vel, "torch.float64"),
                                             _dev(grad_mass, "torch.float64")))
+
+
+def whg_adjoint_schedule(ctx, sm_split: int = -1, tape_bytes: int = 0) -> None:
+    _check(ctx, load().whg_adjoint_schedule(ctx, int(sm_split), int(tape_bytes)))
+
+
+def whg_adjoint_layout(ctx) -> dict:
+    a, b, n = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(ctx, load().whg_adjoint_layout(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)))
+    return {"chain_sms": a.value, "tape_sms": b.value, "tape_buffers": n.value}
 
 
 def whg_synchronize(ctx) -> None:

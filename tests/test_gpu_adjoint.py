@@ -43,6 +43,54 @@ def gpu_grad(whg, ens, target, n, K, gr_mode=1, lanes=0, **kw):
     return loss.cpu().numpy(), gx.cpu().numpy(), gu.cpu().numpy(), gm.cpu().numpy()
 
 
+def test_adjoint_schedules_are_bitwise_identical(whg):
+    """The SM split into green contexts and the tape pool change only where and
+    when the kernels run: on 1024 Solar-System-shaped systems (10 segments of
+    100 steps) the unsplit three-buffer schedule, the split with three
+    buffers (the default), with a buffer per segment and with five (tapes of
+    the missing segments recomputed during the backward half) give bitwise
+    the same losses and gradients, also for a second backward call with other
+    weights, which reuses or recomputes the tapes left by the first."""
+    import torch
+    ens = inputs.solar_ensemble(2024, 1024)
+    T = _targets(ens, 5)
+    S, N, n, K = ens.n_systems, ens.max_planets, 1000, 100
+    seg_bytes = K * 592 * (S // 4) * 32
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    w2 = _t(np.random.default_rng(9).uniform(0.5, 2.0, S))
+    out = {}
+    for name, split, tb in (("off", 0, 0), ("all", -1, -1), ("split3", -1, 0), ("cap5", 64, 5 * seg_bytes)):
+        it = whg.Integrator(S, N, gr_mode=1)
+        whg.whg_init_device(it.ctx, _t(ens.masses), _t(ens.pos), _t(ens.vel), _t(ens.n_planets, torch.int32),
+                            _t(ens.dt))
+        whg.whg_adjoint_schedule(it.ctx, split, tb)
+        loss = torch.empty(S, dtype=torch.float64, device="cuda")
+        whg.whg_adjoint_forward(it.ctx, n, K, _t(T), loss)
+        lay = whg.whg_adjoint_layout(it.ctx)
+        grads = []
+        for w in (None, w2):
+            g = [torch.empty((S, 1 + N, 3), dtype=torch.float64, device="cuda") for _ in range(2)]
+            g.append(torch.empty((S, 1 + N), dtype=torch.float64, device="cuda"))
+            whg.whg_adjoint_backward(it.ctx, w, *g)
+            grads.append([x.cpu().numpy() for x in g])
+        it.synchronize()
+        it.close()
+        out[name] = (loss.cpu().numpy(), grads, lay)
+    assert out["off"][2] == {"chain_sms": 0, "tape_sms": 0, "tape_buffers": 3}
+    for name, nbuf in (("all", 10), ("split3", 3), ("cap5", 5)):
+        lay = out[name][2]
+        assert lay["chain_sms"] >= 64 and lay["chain_sms"] + lay["tape_sms"] == sms, (name, lay)
+        assert lay["tape_buffers"] == nbuf, (name, lay)
+    ref_loss, ref_grads, _ = out["off"]
+    assert np.isfinite(ref_loss).all() and np.isfinite(ref_grads[0][0]).all()
+    for name in ("all", "split3", "cap5"):
+        loss, grads, _ = out[name]
+        assert np.array_equal(loss, ref_loss), name
+        for a, b in zip(grads, ref_grads):
+            for x, y in zip(a, b):
+                assert np.array_equal(x, y), name
+
+
 def gpu_loss(whg, ens, target, n, gr_mode=1, lanes=0):
     it = whg.Integrator(ens.n_systems, ens.max_planets, gr_mode=gr_mode, lanes_per_system=lanes)
     it.init(ens)
@@ -255,3 +303,7 @@ def test_adjoint_state_errors(whg):
     g = torch.empty((4, 3, 3), dtype=torch.float64, device="cuda")
     with pytest.raises(whg.WhgError):
         whg.whg_adjoint_backward(it.ctx, None, g, g, None)
+    for bad in ((-2, -1), (-1, -2)):
+        with pytest.raises(whg.WhgError) as e:
+            whg.whg_adjoint_schedule(it.ctx, *bad)
+        assert e.value.code == whg.WHG_EINVAL
