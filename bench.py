@@ -309,15 +309,15 @@ def measure_adjoint(whg, torch, systems=1024, steps=10000, every=100, seed=4242)
     return res
 
 
-def time_rate(whg, torch, ens, window_s: float, stream, **kw) -> tuple[float, int]:
+def time_rate(whg, torch, ens, window_s: float, stream, min_steps: int = 32, **kw) -> tuple[float, int]:
     """System-steps/s of one Integrator configuration on `ens`, CUDA events
-    on the library's stream over a window of about window_s after a warm-up
-    call of the same length."""
+    on the library's stream over a window of about window_s (and at least
+    min_steps steps) after a warm-up call of the same length."""
     S = ens.n_systems
     it = whg.Integrator(S, ens.max_planets, stream=stream.cuda_stream, **kw)
     try:
         it.init(ens)
-        n = max(32, int(2.4e8 * window_s / S))
+        n = max(min_steps, int(2.4e8 * window_s / S))
         it.step(n)
         it.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -366,14 +366,17 @@ def measure_uneven(whg, torch, systems=1 << 16, steps=20000, seed=303):
     return out
 
 
-def throughput_sweep(whg, torch, sizes=tuple(1 << k for k in range(14, 21)), window_s=0.4, seed=77):
+def throughput_sweep(whg, torch, sizes=tuple(1 << k for k in range(14, 21)), window_s=1.0, min_steps=1000,
+                     seed=77):
     """System-steps/s and FP64 fraction against ensemble size (Solar-System-
     shaped systems, GR on, default solver).  At each size the autotuner picks
     the launch configuration among those that leave results bit for bit
     unchanged (block size, work queue, automatic launch lengths or 100-step
     launches replayed as CUDA graphs of 16; 0.05 s per candidate), then that
-    configuration is timed with CUDA events over a window of about window_s
-    after a warm-up call."""
+    configuration is timed with CUDA events over a window of at least
+    window_s and min_steps steps after a warm-up call of the same length
+    (step time does not depend on the coordinates, so a window stands for
+    the nominal 1e7-step run)."""
     from paper_2307_05683_gb300 import autotune
     base = inputs.solar_ensemble(seed, 4096)
     out = []
@@ -382,7 +385,7 @@ def throughput_sweep(whg, torch, sizes=tuple(1 << k for k in range(14, 21)), win
         ens = base.tile(S)
         best = autotune.tune(ens, gr_mode=1, cache_path=None, window_s=0.05, space="launch")
         cfg = {k: best[k] for k in ("block_size", "queue_steps", "steps_per_launch", "graph_launches")}
-        rate, n = time_rate(whg, torch, ens, window_s, stream, gr_mode=1, **cfg)
+        rate, n = time_rate(whg, torch, ens, window_s, stream, min_steps=min_steps, gr_mode=1, **cfg)
         out.append({"systems": S, "steps": n, "system_steps_per_s": round(rate, 1),
                     "frac": round(rate * fp64_flops(1, False) / 1e12 / FP64_PEAK_TFLOPS, 4),
                     "config": cfg, "candidates_timed": best["tried"]})
