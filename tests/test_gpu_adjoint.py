@@ -290,6 +290,38 @@ def test_adjoint_checkpoint_interval_does_not_change_gradients(whg):
         assert np.array_equal(x, y) and np.array_equal(x, z)
 
 
+@pytest.mark.parametrize("split", [-1, 0])
+def test_adjoint_of_zero_steps_is_the_initial_position_gradient(whg, split):
+    """With no steps the loss is sum_i |x_i - x_0 - T_i|^2 over the initial
+    inertial positions: its gradient is 2 (Q_i - T_i) for planet i and minus
+    their sum for the star, zero for velocities and masses; the adjoint
+    (checkpoint, loss and finish kernels only; split or not) gives that."""
+    import torch
+    ens = inputs.solar_ensemble(36, 48)
+    T = _targets(ens, 6)
+    S, N = ens.n_systems, ens.max_planets
+    it = whg.Integrator(S, N, gr_mode=1)
+    whg.whg_init_device(it.ctx, _t(ens.masses), _t(ens.pos), _t(ens.vel), _t(ens.n_planets, torch.int32),
+                        _t(ens.dt))
+    whg.whg_adjoint_schedule(it.ctx, split, 0)
+    loss = torch.empty(S, dtype=torch.float64, device="cuda")
+    whg.whg_adjoint_forward(it.ctx, 0, 100, _t(T), loss)
+    gx = torch.empty((S, 1 + N, 3), dtype=torch.float64, device="cuda")
+    gu = torch.empty_like(gx)
+    gm = torch.empty((S, 1 + N), dtype=torch.float64, device="cuda")
+    whg.whg_adjoint_backward(it.ctx, None, gx, gu, gm)
+    it.synchronize()
+    it.close()
+    Q = ens.pos[:, 1:] - ens.pos[:, :1]
+    d = 2.0 * (Q - T)
+    want = np.concatenate([-d.sum(axis=1, keepdims=True), d], axis=1)
+    scale = np.abs(want).max()
+    assert np.abs(gx.cpu().numpy() - want).max() <= 1e-13 * scale
+    assert np.array_equal(gu.cpu().numpy(), np.zeros_like(want))
+    assert np.array_equal(gm.cpu().numpy(), np.zeros((S, 1 + N)))
+    assert np.allclose(loss.cpu().numpy(), ((Q - T) ** 2).sum(axis=(1, 2)), rtol=1e-13, atol=0)
+
+
 def test_adjoint_state_errors(whg):
     import torch
     ens = inputs.two_planet_system(0, 4)
