@@ -49,6 +49,9 @@ ALG_FLOPS = {(8, 8, 1): 3464, (8, 8, 0): 3336, (8, 6, 1): 3272, (8, 8, 2): 3536}
 # Halley steps, 8 drifts): with the halley_fp32 option they run on the FP32
 # pipe, and that option's FP64 roofline counts ALG_FLOPS - START_FLOPS.
 START_FLOPS = {(8, 8, 1): 776, (8, 8, 0): 776, (8, 6, 1): 776, (8, 8, 2): 776}
+# The same count for systems of n = 1..8 planets (8-term series, GR on), for
+# ensembles of mixed planet counts; a CPU test keeps it equal to the oracle's.
+ALG_FLOPS_BY_PLANETS = {1: 349, 2: 722, 3: 1119, 4: 1540, 5: 1985, 6: 2454, 7: 2947, 8: 3464}
 
 
 def fp64_flops(gr_mode: int, halley_fp32: bool, newton_terms: int = 8) -> int:
@@ -341,11 +344,14 @@ def measure_uneven(whg, torch, systems=1 << 16, steps=20000, seed=303):
     Rates count every system for every
     step (a frozen system counts but costs nothing once its whole warp is
     frozen); CUDA events on the library's stream after a warm-up of 1600
-    steps."""
+    steps.  The FP64 fraction counts the algorithmic flops of each system's
+    planet count (idle lanes do none), every system every step."""
     ens = inputs.compact_ensemble(seed, systems)
     stream = torch.cuda.Stream()
+    flops = float(np.mean([ALG_FLOPS_BY_PLANETS[int(n)] for n in ens.n_planets]))
     out = {"workload": f"{systems} compact systems, 2..8 planets, stop rules on (1 mutual Hill radius, "
-                       f"100 x largest initial a), GR on, 100-step launches in graphs of 16, {steps} steps"}
+                       f"100 x largest initial a), GR on, 100-step launches in graphs of 16, {steps} steps",
+           "algorithmic_flops_per_system_step": round(flops, 1)}
     for name, lanes, repack in (("packed", 0, None), ("packed_no_repack", 0, False), ("lanes8", 8, None)):
         it = whg.Integrator(systems, 8, gr_mode=1, lanes_per_system=lanes, steps_per_launch=100,
                             graph_launches=16, close_encounter_hill=1.0, eject_factor=100.0,
@@ -361,8 +367,9 @@ def measure_uneven(whg, torch, systems=1 << 16, steps=20000, seed=303):
         ms = e0.elapsed_time(e1)
         _, _, st, _ = it.read_state()
         it.close()
-        out[name] = {"system_steps_per_s": round(systems * steps / (ms / 1e3), 1),
-                     "stopped": int((st != 0).sum())}
+        rate = systems * steps / (ms / 1e3)
+        out[name] = {"system_steps_per_s": round(rate, 1), "stopped": int((st != 0).sum()),
+                     "frac": round(rate * flops / 1e12 / FP64_PEAK_TFLOPS, 4)}
     return out
 
 

@@ -15,6 +15,16 @@ def test_alg_flops_table_matches_oracle_count(orc):
         assert bench.fp64_flops(gr, False, nt) == flops
 
 
+def test_flops_by_planet_count_match_oracle(orc):
+    """The per-planet-count table (mixed ensembles' roofline) equals the
+    oracle's counting build for 1..8 planets, 8-term series, GR on."""
+    bench = importlib.import_module("bench")
+    assert sorted(bench.ALG_FLOPS_BY_PLANETS) == list(range(1, 9))
+    for n, flops in bench.ALG_FLOPS_BY_PLANETS.items():
+        assert orc.count_flops(n, 8, 1)["flops"] == flops, n
+    assert bench.ALG_FLOPS_BY_PLANETS[8] == bench.ALG_FLOPS[(8, 8, 1)]
+
+
 def test_start_phase_count_follows_the_halley_iterations(orc):
     """The starting-phase tally grows by one Halley step's flops per extra
     iteration and is the initial guess alone without Halley steps, so it
