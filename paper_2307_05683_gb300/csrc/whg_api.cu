@@ -773,6 +773,7 @@ namespace {
 // Driver entry points for green contexts, fetched through the runtime so that
 // the library does not link the driver library.
 struct GreenApi {
+    PFN_cuDeviceGet_v2000 device_get = nullptr;
     PFN_cuDeviceGetDevResource_v12040 get_resource = nullptr;
     PFN_cuDevSmResourceSplitByCount_v12040 split = nullptr;
     PFN_cuDevResourceGenerateDesc_v12040 make_desc = nullptr;
@@ -804,7 +805,8 @@ static const GreenApi& green_api()
 {
     static const GreenApi api = [] {
         GreenApi a;
-        a.ok = driver_fn("cuDeviceGetDevResource", 12040, &a.get_resource) &&
+        a.ok = driver_fn("cuDeviceGet", 2000, &a.device_get) &&
+               driver_fn("cuDeviceGetDevResource", 12040, &a.get_resource) &&
                driver_fn("cuDevSmResourceSplitByCount", 12040, &a.split) &&
                driver_fn("cuDevResourceGenerateDesc", 12040, &a.make_desc) &&
                driver_fn("cuGreenCtxCreate", 12040, &a.create) &&
@@ -861,16 +863,18 @@ static bool make_split(whg_ctx* c, int want)
     if (!g.ok) return false;
     if (c->g_chain && c->chain_sms >= want && c->chain_sms < want + 8) return true;
     release_split(c);
+    CUdevice dev = 0;
+    if (g.device_get(&dev, c->device) != CUDA_SUCCESS) return false;
     CUdevResource all{}, part{}, rest{};
-    if (g.get_resource((CUdevice)c->device, &all, CU_DEV_RESOURCE_TYPE_SM) != CUDA_SUCCESS) return false;
+    if (g.get_resource(dev, &all, CU_DEV_RESOURCE_TYPE_SM) != CUDA_SUCCESS) return false;
     unsigned n = 1;
     if (g.split(&part, &n, &all, &rest, 0, (unsigned)want) != CUDA_SUCCESS || n != 1 ||
         rest.sm.smCount < 8)
         return false;
     CUdevResourceDesc dc = nullptr, dt = nullptr;
     bool ok = g.make_desc(&dc, &part, 1) == CUDA_SUCCESS && g.make_desc(&dt, &rest, 1) == CUDA_SUCCESS &&
-              g.create(&c->g_chain, dc, (CUdevice)c->device, CU_GREEN_CTX_DEFAULT_STREAM) == CUDA_SUCCESS &&
-              g.create(&c->g_tape, dt, (CUdevice)c->device, CU_GREEN_CTX_DEFAULT_STREAM) == CUDA_SUCCESS &&
+              g.create(&c->g_chain, dc, dev, CU_GREEN_CTX_DEFAULT_STREAM) == CUDA_SUCCESS &&
+              g.create(&c->g_tape, dt, dev, CU_GREEN_CTX_DEFAULT_STREAM) == CUDA_SUCCESS &&
               g.as_ctx(&c->x_chain, c->g_chain) == CUDA_SUCCESS && g.as_ctx(&c->x_tape, c->g_tape) == CUDA_SUCCESS;
     CUstream s0 = nullptr, s1 = nullptr, s2 = nullptr;
     ok = ok && g.stream_create(&s0, c->g_chain, CU_STREAM_NON_BLOCKING, 0) == CUDA_SUCCESS;
