@@ -83,6 +83,9 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU work of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seed", type=int, default=2024)
+    p.add_argument("--only", choices=["adjoint", "sweep", "uneven"], default=None,
+                   help="run just this one of the extra measurements on one GPU and print its JSON "
+                        "(a short command for profiling its kernels); no benchmark line")
     return p.parse_args()
 
 
@@ -586,10 +589,22 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_only(args):
+    import torch
+    from paper_2307_05683_gb300 import build, whg
+    torch.cuda.set_device(0)
+    build.build()
+    whg.load()
+    fn = {"adjoint": measure_adjoint, "sweep": throughput_sweep, "uneven": measure_uneven}[args.only]
+    print(json.dumps({args.only: fn(whg, torch)}), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.only:
+        run_only(args)
     else:
         run_whg(args)
 
