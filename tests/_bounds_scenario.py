@@ -46,6 +46,15 @@ gu = torch.empty_like(gx)
 gm = torch.empty((300, 9), dtype=torch.float64, device="cuda")
 whg.whg_adjoint_backward(it.ctx, None, gx, gu, gm)
 flags["device_init_adjoint"] = whg.whg_debug_bounds(it.ctx)
+# a tape per segment, computed beside the forward half, and a second backward
+# call with weights (the tape pool of the SM-split schedule)
+whg.whg_init_device(it.ctx, dev(ens.masses), dev(ens.pos), dev(ens.vel), dev(ens.n_planets, torch.int32),
+                    dev(ens.dt))
+whg.whg_adjoint_schedule(it.ctx, -1, -1)
+whg.whg_adjoint_forward(it.ctx, 250, 50, dev(target), loss)
+whg.whg_adjoint_backward(it.ctx, None, gx, gu, gm)
+whg.whg_adjoint_backward(it.ctx, dev(np.linspace(0.5, 2.0, 300)), gx, gu, gm)
+flags["adjoint_tape_pool"] = whg.whg_debug_bounds(it.ctx)
 it.close()
 
 # the allocation-free entry point: mixed planet counts with stop rules, then

@@ -21,7 +21,7 @@ def test_debug_build_index_checks_stay_clear():
                        capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stderr[-3000:]
     flags = json.loads(r.stdout.strip().splitlines()[-1])
-    assert len(flags) == 4 and all(v == 0 for v in flags.values()), flags
+    assert len(flags) == 5 and all(v == 0 for v in flags.values()), flags
 
 
 def test_release_build_reports_no_index_checks():
