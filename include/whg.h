@@ -249,7 +249,10 @@ int whg_adjoint_backward(whg_ctx* ctx, const double* loss_weight, double* grad_p
  *   In the backward half the back kernels, its critical path, then run on
  *   ceil(warps / 4) SMs (rounded up to the partition granularity, 8 SMs on
  *   this GPU), one warp per sub-partition, and the tape kernels on the
- *   remaining SMs, so that the two never share a sub-partition.
+ *   remaining SMs, so that the two never share a sub-partition.  The forward
+ *   half runs on all SMs except for its last two segments, which move to the
+ *   back kernels' SMs while the tape kernels compute the first two tapes the
+ *   backward half needs.
  *   0: no split; the tape kernels run on two side streams beside the back
  *   kernels, wherever the block scheduler puts them.
  *   n > 0: split with n SMs for the back kernels.
@@ -267,9 +270,10 @@ int whg_adjoint_backward(whg_ctx* ctx, const double* loss_weight, double* grad_p
  * Returns WHG_EINVAL for values below -1. */
 int whg_adjoint_schedule(whg_ctx* ctx, int sm_split, long long tape_bytes);
 
-/* After whg_adjoint_forward: SMs of the partition that runs the forward half
- * and the back kernels and of the one that runs the tape kernels (both 0 when
- * unsplit), and the number of tape buffers.  Any pointer may be NULL. */
+/* After whg_adjoint_forward: SMs of the partition that runs the back kernels
+ * (and the forward half's last segments, or all of it with a tape budget) and
+ * of the one that runs the tape kernels (both 0 when unsplit), and the number
+ * of tape buffers.  Any pointer may be NULL. */
 int whg_adjoint_layout(const whg_ctx* ctx, int* chain_sms, int* tape_sms, int* tape_buffers);
 
 /* Wait until all work issued on ctx's stream has finished. */
