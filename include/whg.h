@@ -32,9 +32,12 @@
  * (close encounter, ejection) end a system the same way.
  *
  * Threads and streams: a context is not thread-safe.  All device work of a
- * context is issued on the stream given to whg_create / whg_set_stream (NULL =
- * the legacy default stream).  Calls marked "async" return after enqueueing;
- * calls taking host buffers block until their data has been copied.
+ * context is ordered on the stream given to whg_create / whg_set_stream (NULL =
+ * the legacy default stream): the adjoint's work on its own side streams and
+ * SM partitions starts after what was issued on that stream before the call,
+ * and the stream waits for it before anything issued after the call.  Calls
+ * marked "async" return after enqueueing; calls taking host buffers block
+ * until their data has been copied.
  */
 #ifndef WHG_H
 #define WHG_H
