@@ -761,7 +761,9 @@ namespace {
 // ensemble's warps fill at most half of the GPU at one warp per sub-partition,
 // the SMs are split in two green contexts for the backward half: the back
 // kernels run on the first (4 warps per block: one per sub-partition), the
-// tape kernels on the second, and the two never share an SM.  Optionally
+// tape kernels on the second, and the two never share an SM.  The forward
+// half's last two segments also run on the first partition while the second
+// computes the first two tapes the backward half needs.  Optionally
 // (a tape budget) the tapes of the segments already passed are recomputed
 // during the forward half instead, into a pool of buffers; the forward half
 // then runs on the first partition too.  That measured no faster at a
